@@ -1,0 +1,194 @@
+"""Seeded synthetic CSR workloads.
+
+This module holds no arithmetic of the sketch: it only draws inputs.  Both the
+CUDA path and the CPU oracle are fed from here, so that the two sides see the
+same vectors.  All draws use numpy's PCG64 generator, which gives the same
+numbers on x86-64 and aarch64.
+
+The shapes follow the paper's synthetic settings (Sec. 4: weights UNI(0,1) or
+EXP(1), n+ from 10^2 to 10^6, k from 2^6 to 2^12) at the sizes of the five
+benchmark configurations:
+
+* ``single_vector``   -- one row, n = 10,000 dims, n+ = 1,000 positive entries at
+  uniformly random ids, weights Uniform(0, 1], k = 128.
+* ``lognormal_batch`` -- 4,096 rows, n+ ~ LogNormal(ln 2000, 1) clipped to
+  [10, 200,000], ids uniform without replacement in [0, 2^24) and sorted within
+  the row, weights Exp(1).
+* ``pareto_heavy``    -- 16 rows of n+ = 1,000,000, weights Pareto(alpha=1.2,
+  x_min=1e-3).
+* ``serving_requests`` -- a Poisson request stream, n+ log-uniform in
+  [100, 5e6], weights an equal mixture of Exp(1) and Pareto(1.5), k uniform in
+  {256, 1024, 4096}.
+* ``jaccard_pairs``   -- pairs of rows sharing a fraction of their ids, the
+  shared weights multiplied by a log-normal perturbation.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+ID_SPACE = 1 << 24
+
+
+@dataclass
+class CSR:
+    row_ptr: np.ndarray  # int64 [n_rows + 1]
+    ids: np.ndarray      # int32 [nnz]
+    w: np.ndarray        # float64 [nnz]
+
+    @property
+    def n_rows(self) -> int:
+        return int(self.row_ptr.size - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def row(self, r):
+        lo, hi = int(self.row_ptr[r]), int(self.row_ptr[r + 1])
+        return self.ids[lo:hi], self.w[lo:hi]
+
+    def take_rows(self, rows) -> "CSR":
+        rows = np.asarray(rows, dtype=np.int64)
+        lens = self.row_ptr[rows + 1] - self.row_ptr[rows]
+        rp = np.zeros(rows.size + 1, dtype=np.int64)
+        np.cumsum(lens, out=rp[1:])
+        ids = np.concatenate([self.row(r)[0] for r in rows]) if rows.size else np.zeros(0, np.int32)
+        w = np.concatenate([self.row(r)[1] for r in rows]) if rows.size else np.zeros(0, np.float64)
+        return CSR(rp, ids.astype(np.int32), w.astype(np.float64))
+
+
+def _distinct_ids(rng, n, space):
+    """n distinct ids drawn uniformly from [0, space), sorted."""
+    if n > space:
+        raise ValueError("more ids than the id space")
+    if n * 4 > space:
+        return np.sort(rng.permutation(space)[:n]).astype(np.int32)
+    got = np.unique(rng.integers(0, space, size=int(n * 1.1) + 16))
+    while got.size < n:
+        got = np.unique(np.concatenate([got, rng.integers(0, space, size=n)]))
+    if got.size > n:
+        got = np.sort(rng.choice(got, size=n, replace=False))
+    return got.astype(np.int32)
+
+
+def from_rows(rows) -> CSR:
+    """Build a CSR from a list of (ids, weights) pairs."""
+    lens = np.array([len(r[0]) for r in rows], dtype=np.int64)
+    rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    ids = np.concatenate([np.asarray(r[0], np.int32) for r in rows]) if rows else np.zeros(0, np.int32)
+    w = np.concatenate([np.asarray(r[1], np.float64) for r in rows]) if rows else np.zeros(0, np.float64)
+    return CSR(rp, ids.astype(np.int32), w.astype(np.float64))
+
+
+def single_vector(seed=1, n_dims=10_000, n_pos=1_000) -> CSR:
+    rng = np.random.default_rng(seed)
+    ids = np.sort(rng.choice(n_dims, size=n_pos, replace=False)).astype(np.int32)
+    w = 1.0 - rng.random(n_pos)  # Uniform(0, 1]
+    return from_rows([(ids, w)])
+
+
+def lognormal_lengths(rng, n_rows, median=2000.0, sigma=1.0, lo=10, hi=200_000):
+    n = np.rint(rng.lognormal(np.log(median), sigma, size=n_rows)).astype(np.int64)
+    return np.clip(n, lo, hi)
+
+
+def lognormal_batch(seed=1, n_rows=4096, median=2000.0, sigma=1.0, lo=10, hi=200_000) -> CSR:
+    rng = np.random.default_rng(seed)
+    lens = lognormal_lengths(rng, n_rows, median, sigma, lo, hi)
+    rows = []
+    for n in lens:
+        ids = _distinct_ids(rng, int(n), ID_SPACE)
+        w = rng.standard_exponential(int(n))
+        rows.append((ids, w))
+    return from_rows(rows)
+
+
+def pareto_weights(rng, n, alpha, x_min):
+    return x_min * (1.0 + rng.pareto(alpha, size=n))
+
+
+def pareto_heavy(seed=1, n_rows=16, n_pos=1_000_000, alpha=1.2, x_min=1e-3) -> CSR:
+    rng = np.random.default_rng(seed)
+    rows = []
+    for _ in range(n_rows):
+        ids = _distinct_ids(rng, n_pos, ID_SPACE)
+        rows.append((ids, pareto_weights(rng, n_pos, alpha, x_min)))
+    return from_rows(rows)
+
+
+def uniform_rows(seed, n_rows, n_pos, space=ID_SPACE, weight="uniform") -> CSR:
+    """Rows of fixed length n_pos (int or array) with Uniform(0,1] or Exp(1) weights."""
+    rng = np.random.default_rng(seed)
+    lens = np.broadcast_to(np.asarray(n_pos, dtype=np.int64), (n_rows,))
+    rows = []
+    for n in lens:
+        ids = _distinct_ids(rng, int(n), space)
+        w = (1.0 - rng.random(int(n))) if weight == "uniform" else rng.standard_exponential(int(n))
+        rows.append((ids, w))
+    return from_rows(rows)
+
+
+def jaccard_pairs(seed, n_pairs, n_pos, shared=0.5, sigma=0.2, space=ID_SPACE):
+    """Two CSR batches A, B: row p of B shares a fraction `shared` of row p of A's ids.
+
+    Shared entries get the A weight times exp(N(0, sigma^2)); the rest are fresh ids
+    with Exp(1) weights.
+    """
+    rng = np.random.default_rng(seed)
+    ra, rb = [], []
+    for _ in range(n_pairs):
+        ids = _distinct_ids(rng, 2 * n_pos, space)
+        rng.shuffle(ids)
+        a_ids = ids[:n_pos]
+        n_sh = int(round(shared * n_pos))
+        b_ids = np.concatenate([a_ids[:n_sh], ids[n_pos:2 * n_pos - n_sh]])
+        a_w = rng.standard_exponential(n_pos)
+        b_w = np.concatenate([a_w[:n_sh] * np.exp(rng.normal(0.0, sigma, n_sh)),
+                              rng.standard_exponential(n_pos - n_sh)])
+        oa, ob = np.argsort(a_ids), np.argsort(b_ids)
+        ra.append((a_ids[oa], a_w[oa]))
+        rb.append((b_ids[ob], b_w[ob]))
+    return from_rows(ra), from_rows(rb)
+
+
+@dataclass
+class Request:
+    t_arrive: float
+    kind: str        # "sketch" | "jaccard" | "cardinality"
+    k: int
+    csr: CSR = None
+    pair: tuple = None   # (handle_a, handle_b) for jaccard
+    handle: int = -1     # for cardinality
+
+
+def serving_requests(seed=1, n_requests=2000, rate=20_000.0, n_lo=100, n_hi=5_000_000,
+                     ks=(256, 1024, 4096), query_frac=0.3, max_nnz=None):
+    """A Poisson stream of sketch requests plus Jaccard / cardinality queries.
+
+    Queries refer to earlier sketch requests by their index in the stream.
+    ``max_nnz`` caps n+ (used by tests to keep the case small).
+    """
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    hi = n_hi if max_nnz is None else min(n_hi, max_nnz)
+    reqs = []
+    sketch_idx = []
+    for q in range(n_requests):
+        if sketch_idx and rng.random() < query_frac:
+            if rng.random() < 0.5 and len(sketch_idx) >= 2:
+                a, b = rng.choice(sketch_idx, size=2, replace=False)
+                reqs.append(Request(float(t[q]), "jaccard", 0, pair=(int(a), int(b))))
+            else:
+                reqs.append(Request(float(t[q]), "cardinality", 0, handle=int(rng.choice(sketch_idx))))
+            continue
+        n = int(np.exp(rng.uniform(np.log(n_lo), np.log(hi))))
+        ids = _distinct_ids(rng, n, ID_SPACE)
+        if rng.random() < 0.5:
+            w = rng.standard_exponential(n)
+        else:
+            w = pareto_weights(rng, n, 1.5, 1.0)
+        k = int(rng.choice(ks))
+        reqs.append(Request(float(t[q]), "sketch", k, csr=from_rows([(ids, w)])))
+        sketch_idx.append(q)
+    return reqs
