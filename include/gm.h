@@ -1,0 +1,169 @@
+/*
+ * gm.h -- C-ABI of libgm, the GB300 (sm_103a) k-register Gumbel-Max sketch.
+ *
+ * Paper: Y. Zhang, P. Wang, Y. Qi, K. Cheng, J. Zhao, G. Tian, X. Guan,
+ * "Fast Gumbel-Max Sketch and its Applications", arXiv 2302.05176.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller, unless a
+ *     parameter says "host".  The library never frees them and never keeps
+ *     them after the call returns.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream).  The return value only reports
+ *     errors found on the host before launch (bad sizes, null pointers, a
+ *     workspace that is too small, a failed launch).  Errors found on the
+ *     device are recorded in the workspace and read back by gm_status().
+ *   - The library allocates no memory.  Scratch space comes from a caller
+ *     workspace whose size gm_sketch_workspace_bytes() reports.  Calls that
+ *     share a workspace must be ordered (same stream, or synchronised).
+ *   - All functions are thread-safe as long as concurrent calls use distinct
+ *     workspaces.
+ *
+ * The sketch (Sec. 1, Eq. sjv and Eq. yjpi): for a non-negative vector v and
+ * k registers, register j holds
+ *     y_j = min_{i : v_i > 0} b_{i,j},   s_j = the i attaining it,
+ * where b_{i,1..k} are element i's k arrival times, generated in ascending order
+ * as exponential order statistics (Sec. 2.2, Eq. biz_dis / biz_biz-1) and
+ * spread over the k registers by a Fisher-Yates shuffle (same section).
+ * Arrival z (0-based) of element id with weight v, for a given (k, seed):
+ *     (w0,w1,w2,w3) = Philox4x32-10(key = (seed_lo, seed_hi), ctr = (id, z, 0, 0))
+ *     u   = (2 * ((w1:w0) >> 12) + 1) * 2^-53            exact, in (0, 1)
+ *     E   = RN(-ln u)
+ *     t_z = RN(E * RN(1 / (k - z)))
+ *     S_z = RN(t_0 + ... + t_z)        (the sum formed exactly, rounded once)
+ *     b_z = RN(S_z * RN(1 / v))
+ *     J   = z + floor((w3:w2) * (k - z) / 2^64);  swap(pi[z], pi[J]);  server = pi[z]
+ * Ties in a register go to the smaller id.  An unfilled register reads
+ * y = +inf, s = -1.  Zero weights take no part (N^+ of Sec. 1).
+ * Results do not depend on the pruning bound, the launch shape or the
+ * algorithm variant: gm_sketch (FastGM) and gm_sketch_plain (all k n+
+ * arrivals) return the same registers.
+ */
+#ifndef GM_H
+#define GM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define GM_OK 0
+#define GM_EINVAL 1   /* an argument is out of range (see each function)           */
+#define GM_ENOMEM 2   /* the workspace is smaller than gm_*_workspace_bytes() says  */
+#define GM_ECUDA 3    /* a CUDA launch or query failed                              */
+#define GM_ETIMEOUT 4 /* a bounded device-side retry loop gave up (device status)   */
+#define GM_EDATA 5    /* invalid input data found on the device (device status)     */
+
+/* ---- flags for gm_sketch ------------------------------------------------ */
+/* Validate the CSR on the device: row_ptr[0] == 0, non-decreasing, row_ptr[n_rows]
+ * == nnz, ids >= 0, weights finite and >= 0.  A violation sets GM_EDATA in the
+ * device status (gm_status); the registers of an invalid row are unspecified. */
+#define GM_FLAG_VALIDATE (1u << 0)
+/* Initial pruning bound per row (Sec. 2.2 FastSearch / FastPrune).  Any bound
+ * gives the same registers; it only changes how many arrivals are generated. */
+#define GM_BOUND_CLOSED (0u << 4)  /* closed-form quantile of y* (default)          */
+#define GM_BOUND_NONE (1u << 4)    /* no initial bound: prune only by the running y* */
+#define GM_BOUND_LEARNED (2u << 4) /* per-row bound from a trained model (gm_model_*) */
+#define GM_BOUND_MASK (3u << 4)
+
+/* ---- device-side counters, read back by gm_status ------------------------- */
+typedef struct gm_stats {
+  uint64_t arrivals;        /* arrivals generated (light + heavy paths)               */
+  uint64_t elements;        /* positive elements visited                               */
+  uint64_t screened_out;    /* elements whose first arrival exceeded the row bound      */
+  uint64_t heavy_elements;  /* elements streamed by the warp-cooperative path          */
+  uint64_t rows_escalated;  /* row passes repeated with a larger bound (unfilled rows) */
+  uint64_t cas_retries;     /* register compare-and-swap retries                        */
+  uint32_t status;          /* GM_OK, GM_EDATA or GM_ETIMEOUT                           */
+  uint32_t reserved;
+} gm_stats;
+
+/* Bytes of workspace gm_sketch / gm_sketch_plain need for this problem.
+ * Returns 0 if the arguments are out of range. */
+size_t gm_sketch_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k, uint32_t flags);
+
+/*
+ * gm_sketch -- FastGM (Algorithm 1, Sec. 2.2) over a batch of CSR rows.
+ *
+ *   row_ptr  int64[n_rows + 1]   row r owns elements [row_ptr[r], row_ptr[r+1])
+ *   ids      int32[nnz]          element ids (>= 0); ids within a row should be distinct
+ *   w        float64[nnz]        weights (finite, >= 0; zero weights are skipped)
+ *   n_rows   >= 0
+ *   nnz      == row_ptr[n_rows] (row bounds are clamped to [0, nnz] on the device)
+ *   k        number of registers, 1 <= k <= GM_MAX_K
+ *   seed     64-bit key of the arrival streams (sketches compare only under one seed)
+ *   flags    GM_FLAG_* | GM_BOUND_*
+ *   s_out    int32[n_rows * k]   row-major: register j of row r at r * k + j
+ *   y_out    float64[n_rows * k]
+ *   workspace / workspace_bytes  device scratch, >= gm_sketch_workspace_bytes(...)
+ *   stream   cudaStream_t
+ * Returns GM_OK, GM_EINVAL (bad sizes / null pointers / k out of range),
+ * GM_ENOMEM (workspace too small) or GM_ECUDA.
+ */
+#define GM_MAX_K 4096
+int gm_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
+              int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
+              size_t workspace_bytes, void* stream);
+
+/*
+ * gm_sketch_plain -- the straightforward O(k n+) sketch (Sec. 1, "the
+ * straightforward method"): every positive element generates all k arrivals.
+ * Same arguments, same output as gm_sketch; it exists as the baseline FastGM
+ * is measured against.  `flags` accepts GM_FLAG_VALIDATE only.
+ */
+int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
+                    int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * gm_status -- wait for the work queued on `stream`, then copy the device
+ * status and counters of the last call that used `workspace` into *stats
+ * (host pointer, may be NULL) and return the device status (GM_OK, GM_EDATA
+ * or GM_ETIMEOUT), or GM_ECUDA if the copy fails.  Blocks the calling thread.
+ */
+int gm_status(const void* workspace, gm_stats* stats, void* stream);
+
+/*
+ * gm_jaccard -- probability-Jaccard estimates (Sec. 1; unbiased, variance
+ * J(1-J)/k, Sec. 2.4):  out[p] = (1/k) * #{ j : s_a[p k + j] == s_b[p k + j] >= 0 }.
+ *   s_a, s_b int32[n_pairs * k]  (the caller gathers the two sketches of each pair
+ *                                 into row p of s_a and s_b; both under one (k, seed))
+ *   out      float64[n_pairs]
+ * Unfilled registers (s = -1) never match.  Returns GM_EINVAL if k < 1 or
+ * n_pairs < 0.
+ */
+int gm_jaccard(const int32_t* s_a, const int32_t* s_b, int64_t n_pairs, int32_t k, double* out, void* stream);
+
+/*
+ * gm_cardinality -- weighted-cardinality estimates (Lemiesz's estimator,
+ * Sec. 1 and the Sec. 2.4 theorem):  out[r] = (k - 1) / sum_j y[r k + j].
+ *   y   float64[n_rows * k],  out float64[n_rows]
+ * A row with an unfilled register (y = +inf) estimates 0.  The sum is formed in
+ * FP64 in an order of the library's choosing (relative difference to any other
+ * order <= k * 2^-53).  Returns GM_EINVAL if k < 2 or n_rows < 0.
+ */
+int gm_cardinality(const double* y, int32_t n_rows, int32_t k, double* out, void* stream);
+
+/*
+ * gm_merge -- union of sketches (Sec. 2.3 Mergeability): register-wise minimum
+ * of (y, s), ties to the smaller id, unfilled (+inf, -1) losing to anything.
+ *   s_a, y_a, s_b, y_b  [n_regs] inputs;  s_out, y_out [n_regs] outputs (may alias
+ *   either input).  Returns GM_EINVAL if n_regs < 0.
+ */
+int gm_merge(const int32_t* s_a, const double* y_a, const int32_t* s_b, const double* y_b, int64_t n_regs,
+             int32_t* s_out, double* y_out, void* stream);
+
+/* Human-readable text of a status code (static storage, never NULL). */
+const char* gm_strerror(int code);
+
+/* Library version string, e.g. "libgm 0.1 sm_103a" (static storage). */
+const char* gm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GM_H */

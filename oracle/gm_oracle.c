@@ -22,8 +22,9 @@
  * Readings of the paper fixed here (the paper leaves them open):
  *   R1  RandUNI / RandInt (Algorithm 1) are one Philox4x32-10 call (Salmon et al.,
  *       SC'11) per arrival: key = (seed_lo, seed_hi), counter = (id, z, 0, 0)
- *       with z the 0-based step.  Words 0,1 give m = (w1:w0) >> 11 and
- *       u = (2m+1) * 2^-54, which is never 0 or 1.  Words 2,3 give the 64-bit
+ *       with z the 0-based step.  Words 0,1 give the 52-bit m = (w1:w0) >> 12
+ *       and u = (2m+1) * 2^-53: exact in double (2m+1 < 2^53) and never 0 or 1,
+ *       the open-interval uniform RandUNI(0,1) asks for.  Words 2,3 give the 64-bit
  *       r and RandInt(z, k) = z + floor(r * (k - z) / 2^64).
  *   R2  Rounding: E = RN(-ln u) (here: libm log), C_z = RN(1/(k-z)),
  *       t_z = RN(E * C_z), S_z = RN(t_0 + ... + t_z) with the sum formed
@@ -86,9 +87,9 @@ static void arrival_words(uint64_t seed, int32_t id, uint32_t z, uint32_t w[4]) 
 /* u in (0,1) from words 0,1 (reading R1); exact in double. */
 double gmo_uniform_from_words(uint32_t w0, uint32_t w1) {
   uint64_t x = ((uint64_t)w1 << 32) | (uint64_t)w0;
-  uint64_t m = x >> 11;
-  if (g_mutation == 5) m = x >> 12; /* planted: drop a bit of the uniform */
-  return ldexp((double)(2 * m + 1), -54);
+  uint64_t m = x >> 12;
+  if (g_mutation == 5) m = x >> 13; /* planted: drop a bit of the uniform */
+  return ldexp((double)(2 * m + 1), -53);
 }
 
 /* RandInt(z, k) from words 2,3 (reading R1): uniform in [z, k). */
@@ -102,7 +103,7 @@ int32_t gmo_randint_from_words(uint32_t w2, uint32_t w3, int32_t z, int32_t k) {
  * Exact accumulator for reading R2.  value = sum_i limb[i] * 2^(64 i - 160).
  * It holds exactly any sum of non-negative doubles whose lowest mantissa bit is
  * at least 2^-160 and whose total stays below 2^90.  The method's terms lie in
- * [2^-71, 2^6) (E >= 2^-55, C >= 2^-16) and a stream sums at most 65536 of them,
+ * [2^-70, 2^6) (E >= 2^-53, C >= 2^-16) and a stream sums at most 65536 of them,
  * so every prefix sum the method forms is exact here.
  * ------------------------------------------------------------------------- */
 typedef struct {

@@ -47,15 +47,19 @@ def pin_philox_kat():
 
 def pin_uniform_and_randint():
     fails = []
-    if oracle.uniform_from_words(0, 0) != 2.0 ** -54:
-        fails.append("u(0,0) != 2^-54")
-    if oracle.uniform_from_words(0xFFFFFFFF, 0xFFFFFFFF) != 1.0 - 2.0 ** -54:
-        fails.append("u(max) != 1 - 2^-54")
-    # the top 53 bits of (w1:w0) define m; u = (2m+1) 2^-54
-    x = 0x123456789ABCDEF0
-    m = x >> 11
-    if oracle.uniform_from_words(x & 0xFFFFFFFF, x >> 32) != (2 * m + 1) * 2.0 ** -54:
-        fails.append("u is not (2m+1)2^-54 of the top 53 bits")
+    lo = oracle.uniform_from_words(0, 0)
+    hi = oracle.uniform_from_words(0xFFFFFFFF, 0xFFFFFFFF)
+    if lo != 2.0 ** -53 or not (0.0 < lo):
+        fails.append("u(0,0) != 2^-53")
+    if hi != 1.0 - 2.0 ** -53 or not (hi < 1.0):
+        fails.append("u(max) != 1 - 2^-53 (must stay below 1)")
+    # the top 52 bits of (w1:w0) define m; u = (2m+1) 2^-53, exactly
+    from fractions import Fraction
+    for x in (0x123456789ABCDEF0, 0xFFFFFFFFFFFFF000, 0x8000000000000000, 0x0000000000001FFF):
+        m = x >> 12
+        got = oracle.uniform_from_words(x & 0xFFFFFFFF, x >> 32)
+        if Fraction(got) != Fraction(2 * m + 1, 2 ** 53):
+            fails.append("u(%x) is not exactly (2m+1)2^-53" % x)
     # RandInt(z, k) = z + floor(r (k - z) / 2^64)
     for (r, z, k) in [(0, 3, 10), (2 ** 64 - 1, 3, 10), (2 ** 63, 0, 7), (0x5555555555555555, 2, 5)]:
         want = z + (r * (k - z)) // 2 ** 64
