@@ -1,0 +1,184 @@
+"""Thin Python binding of libgm (include/gm.h): argument marshalling only.
+
+Every step of the sketch runs inside libgm's CUDA kernels; this module only
+passes device pointers (torch tensors) and sizes through the C-ABI, allocates
+outputs and workspaces with torch, and turns status codes into exceptions.
+There is no fallback: if the library is missing, every call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libgm.so")
+
+GM_OK, GM_EINVAL, GM_ENOMEM, GM_ECUDA, GM_ETIMEOUT, GM_EDATA = 0, 1, 2, 3, 4, 5
+GM_FLAG_VALIDATE = 1 << 0
+GM_BOUND_CLOSED = 0 << 4
+GM_BOUND_NONE = 1 << 4
+GM_BOUND_LEARNED = 2 << 4
+GM_MAX_K = 4096
+
+
+class GmError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (code %d)" % (what, strerror(code) if _lib else "libgm", code))
+        self.code = code
+
+
+class gm_stats(ctypes.Structure):
+    _fields_ = [("arrivals", ctypes.c_uint64), ("elements", ctypes.c_uint64), ("screened_out", ctypes.c_uint64),
+                ("heavy_elements", ctypes.c_uint64), ("rows_escalated", ctypes.c_uint64),
+                ("cas_retries", ctypes.c_uint64), ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """Load libgm.so (built in-tree by paper_2302_05176_gb300.build / __graft_entry__.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgm.so is missing at %s: run __graft_entry__.build() first" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.gm_sketch_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32]
+        L.gm_sketch_workspace_bytes.restype = ctypes.c_size_t
+        sk = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32,
+              _vp, _vp, _vp, ctypes.c_size_t, _vp]
+        L.gm_sketch.argtypes = sk
+        L.gm_sketch_plain.argtypes = sk
+        L.gm_status.argtypes = [_vp, ctypes.POINTER(gm_stats), _vp]
+        L.gm_jaccard.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp]
+        L.gm_cardinality.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
+        L.gm_merge.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]
+        L.gm_strerror.argtypes = [ctypes.c_int]
+        L.gm_strerror.restype = ctypes.c_char_p
+        L.gm_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def strerror(code):
+    return lib().gm_strerror(int(code)).decode()
+
+
+def version():
+    return lib().gm_version().decode()
+
+
+def _stream_handle(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def _need_cuda(t, dtype, name):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous CUDA %s tensor" % (name, dtype))
+
+
+def _check(rc, what):
+    if rc != GM_OK:
+        raise GmError(rc, what)
+
+
+def sketch_workspace_bytes(n_rows, nnz, k, flags=0):
+    n = lib().gm_sketch_workspace_bytes(int(n_rows), int(nnz), int(k), int(flags))
+    if n == 0:
+        raise GmError(GM_EINVAL, "gm_sketch_workspace_bytes")
+    return n
+
+
+def workspace(n_rows, nnz, k, flags=0, device=None):
+    return torch.empty(sketch_workspace_bytes(n_rows, nnz, k, flags), dtype=torch.uint8,
+                       device=device or torch.device("cuda"))
+
+
+def _sketch(fn, name, row_ptr, ids, w, k, seed, flags, s_out, y_out, ws, stream):
+    _need_cuda(row_ptr, torch.int64, "row_ptr")
+    _need_cuda(ids, torch.int32, "ids")
+    _need_cuda(w, torch.float64, "w")
+    n_rows = row_ptr.numel() - 1
+    nnz = ids.numel()
+    if w.numel() != nnz:
+        raise ValueError("ids and w differ in length")
+    dev = row_ptr.device
+    if s_out is None:
+        s_out = torch.empty((n_rows, k), dtype=torch.int32, device=dev)
+    if y_out is None:
+        y_out = torch.empty((n_rows, k), dtype=torch.float64, device=dev)
+    _need_cuda(s_out, torch.int32, "s_out")
+    _need_cuda(y_out, torch.float64, "y_out")
+    if ws is None:
+        ws = workspace(n_rows, nnz, k, flags, dev)
+    rc = fn(_ptr(row_ptr), _ptr(ids), _ptr(w), n_rows, nnz, int(k), int(seed) & 0xFFFFFFFFFFFFFFFF, int(flags),
+            _ptr(s_out), _ptr(y_out), _ptr(ws), ws.numel(), _stream_handle(stream))
+    _check(rc, name)
+    return s_out, y_out, ws
+
+
+def gm_sketch(row_ptr, ids, w, k, seed, flags=0, s_out=None, y_out=None, ws=None, stream=None):
+    """FastGM over CSR rows (device tensors) -> (s [n_rows,k] int32, y [n_rows,k] f64, workspace)."""
+    return _sketch(lib().gm_sketch, "gm_sketch", row_ptr, ids, w, k, seed, flags, s_out, y_out, ws, stream)
+
+
+def gm_sketch_plain(row_ptr, ids, w, k, seed, flags=0, s_out=None, y_out=None, ws=None, stream=None):
+    """The O(k n+) sketch; same output as gm_sketch."""
+    return _sketch(lib().gm_sketch_plain, "gm_sketch_plain", row_ptr, ids, w, k, seed, flags, s_out, y_out, ws,
+                   stream)
+
+
+def gm_status(ws, stream=None):
+    """Synchronise the stream and return (device status code, counters dict)."""
+    st = gm_stats()
+    rc = lib().gm_status(_ptr(ws), ctypes.byref(st), _stream_handle(stream))
+    if rc == GM_ECUDA:
+        raise GmError(rc, "gm_status")
+    return rc, st.as_dict()
+
+
+def gm_jaccard(s_a, s_b, out=None, stream=None):
+    _need_cuda(s_a, torch.int32, "s_a")
+    _need_cuda(s_b, torch.int32, "s_b")
+    if s_a.shape != s_b.shape or s_a.dim() != 2:
+        raise ValueError("s_a and s_b must both be [n_pairs, k]")
+    n, k = s_a.shape
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=s_a.device)
+    _check(lib().gm_jaccard(_ptr(s_a), _ptr(s_b), n, k, _ptr(out), _stream_handle(stream)), "gm_jaccard")
+    return out
+
+
+def gm_cardinality(y, out=None, stream=None):
+    _need_cuda(y, torch.float64, "y")
+    n, k = y.shape
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=y.device)
+    _check(lib().gm_cardinality(_ptr(y), n, k, _ptr(out), _stream_handle(stream)), "gm_cardinality")
+    return out
+
+
+def gm_merge(s_a, y_a, s_b, y_b, s_out=None, y_out=None, stream=None):
+    for t, d, nm in ((s_a, torch.int32, "s_a"), (s_b, torch.int32, "s_b"), (y_a, torch.float64, "y_a"),
+                     (y_b, torch.float64, "y_b")):
+        _need_cuda(t, d, nm)
+    s_out = torch.empty_like(s_a) if s_out is None else s_out
+    y_out = torch.empty_like(y_a) if y_out is None else y_out
+    _check(lib().gm_merge(_ptr(s_a), _ptr(y_a), _ptr(s_b), _ptr(y_b), s_a.numel(), _ptr(s_out), _ptr(y_out),
+                          _stream_handle(stream)), "gm_merge")
+    return s_out, y_out
+
+
+def to_device(csr, device="cuda"):
+    """Copy a workloads.CSR to device tensors (row_ptr, ids, w)."""
+    return (torch.from_numpy(csr.row_ptr).to(device), torch.from_numpy(csr.ids).to(device),
+            torch.from_numpy(csr.w).to(device))

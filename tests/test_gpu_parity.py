@@ -1,0 +1,191 @@
+"""CUDA path (through the C-ABI) against the CPU oracle, element by element.
+
+Tolerance (from the definition in include/gm.h): both sides form the same exact
+sums and correctly rounded products and differ only in ln(u); register values
+agree within 4 ulp, register ids exactly except at near-ties (the oracle's two
+best candidates within 1e-12 relative), which are counted.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2302_05176_gb300 import gm
+from paper_2302_05176_gb300 import workloads as W
+from paper_2302_05176_gb300.parity import compare_sketch
+
+pytestmark = pytest.mark.gpu
+
+
+def run(fn, X, k, seed, flags=gm.GM_FLAG_VALIDATE):
+    rp, ids, w = gm.to_device(X)
+    s, y, ws = fn(rp, ids, w, k, seed, flags=flags)
+    code, stats = gm.gm_status(ws)
+    assert code == gm.GM_OK, gm.strerror(code)
+    return s.cpu().numpy(), y.cpu().numpy(), stats
+
+
+def check(X, k, seed, fns=(gm.gm_sketch, gm.gm_sketch_plain), flags=gm.GM_FLAG_VALIDATE):
+    s_ref, y_ref, y2_ref = oracle.sketch(X.row_ptr, X.ids, X.w, k, seed, want_y2=True)
+    outs = []
+    for fn in fns:
+        s, y, stats = run(fn, X, k, seed, flags=flags if fn is gm.gm_sketch else flags & gm.GM_FLAG_VALIDATE)
+        rep = compare_sketch(s, y, s_ref, y_ref, y2_ref)
+        assert rep["ok"], (fn.__name__, rep)
+        outs.append((s, y, stats, rep))
+    # FastGM and the plain sketch use the same device arithmetic: bit-identical
+    if len(outs) == 2:
+        assert np.array_equal(outs[0][0], outs[1][0])
+        assert np.array_equal(outs[0][1].view(np.int64), outs[1][1].view(np.int64))
+    return outs
+
+
+def test_single_vector_k128():
+    X = W.single_vector(seed=1)
+    outs = check(X, 128, 1)
+    assert outs[0][2]["arrivals"] < 0.2 * outs[1][2]["arrivals"]  # FastGM prunes
+
+
+@pytest.mark.parametrize("k", [1, 2, 7, 31, 32, 33, 64, 257, 1024])
+def test_ragged_rows(k):
+    rng = np.random.default_rng(k)
+    lens = [0, 1, 2, 3, 5, 17, 31, 32, 33, 100, 255, 256, 257, 600, 1500]
+    rows = []
+    for i, n in enumerate(lens):
+        ids = np.sort(rng.choice(1 << 24, size=n, replace=False)).astype(np.int32)
+        if i % 3 == 0:
+            wts = 1.0 - rng.random(n)
+        elif i % 3 == 1:
+            wts = rng.standard_exponential(n)
+        else:
+            wts = W.pareto_weights(rng, n, 1.2, 1e-3)
+        rows.append((ids, wts))
+    check(W.from_rows(rows), k, 1234 + k)
+
+
+@pytest.mark.parametrize("k", [256, 4096])
+def test_lognormal_small_batch(k):
+    X = W.lognormal_batch(seed=5, n_rows=24, median=300.0, hi=3000)
+    check(X, k, 77)
+
+
+def test_edge_weights_and_ids():
+    rows = [
+        (np.array([0], np.int32), np.array([1.0])),                                  # single element, id 0
+        (np.array([5, 6, 7], np.int32), np.array([0.0, 0.0, 0.0])),                  # all zero -> unfilled
+        (np.array([2**31 - 1, 3], np.int32), np.array([1e-300, 1e300])),             # extreme weights
+        (np.array([10, 11, 12, 13], np.int32), np.array([1.0, 1e-12, 1e12, 0.5])),  # dynamic range
+        (np.array([], np.int32), np.array([])),                                      # empty row
+        (np.array([9, 8], np.int32), np.array([2.0, 2.0])),                          # unsorted ids
+    ]
+    for k in (1, 3, 64, 1000):
+        check(W.from_rows(rows), k, 99)
+
+
+def test_bound_modes_agree():
+    X = W.lognormal_batch(seed=9, n_rows=16, median=400.0, hi=2000)
+    k = 512
+    s0, y0, st0 = run(gm.gm_sketch, X, k, 3, flags=gm.GM_BOUND_CLOSED)
+    s1, y1, st1 = run(gm.gm_sketch, X, k, 3, flags=gm.GM_BOUND_NONE)
+    assert np.array_equal(s0, s1) and np.array_equal(y0.view(np.int64), y1.view(np.int64))
+    assert st0["arrivals"] < st1["arrivals"]
+
+
+def test_seed_changes_sketch_and_repeat_is_deterministic():
+    X = W.lognormal_batch(seed=2, n_rows=8, median=200.0, hi=800)
+    a = run(gm.gm_sketch, X, 256, 1)
+    b = run(gm.gm_sketch, X, 256, 1)
+    c = run(gm.gm_sketch, X, 256, 2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.int64), b[1].view(np.int64))
+    assert not np.array_equal(a[0], c[0])
+
+
+def test_validation_reports_bad_data():
+    ws = gm.workspace(1, 1000, 16)  # big enough for every call below
+    for ids_, w_ in (([1, 2], [1.0, -2.0]), ([1, -2], [1.0, 2.0]), ([1, 2], [1.0, float("nan")]),
+                     ([1, 2], [float("inf"), 1.0])):
+        bad = W.from_rows([(np.array(ids_, np.int32), np.array(w_))])
+        rp, ids, w = gm.to_device(bad)
+        gm.gm_sketch(rp, ids, w, 16, 1, flags=gm.GM_FLAG_VALIDATE, ws=ws)
+        assert gm.gm_status(ws)[0] == gm.GM_EDATA
+    # row_ptr that does not end at nnz
+    rp = torch.tensor([0, 1], dtype=torch.int64, device="cuda")
+    ids = torch.tensor([3, 4], dtype=torch.int32, device="cuda")
+    w = torch.tensor([1.0, 1.0], dtype=torch.float64, device="cuda")
+    gm.gm_sketch(rp, ids, w, 16, 1, flags=gm.GM_FLAG_VALIDATE, ws=ws)
+    assert gm.gm_status(ws)[0] == gm.GM_EDATA
+    # a good call through the same workspace is clean again
+    good = W.single_vector(seed=3)
+    rp, ids, w = gm.to_device(good)
+    gm.gm_sketch(rp, ids, w, 16, 1, flags=gm.GM_FLAG_VALIDATE, ws=ws)
+    assert gm.gm_status(ws)[0] == gm.GM_OK
+
+
+def test_host_errors():
+    X = W.single_vector(seed=1)
+    rp, ids, w = gm.to_device(X)
+    with pytest.raises(gm.GmError):
+        gm.gm_sketch(rp, ids, w, 0, 1)
+    with pytest.raises(gm.GmError):
+        gm.gm_sketch(rp, ids, w, gm.GM_MAX_K + 1, 1)
+    tiny = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gm.GmError):
+        gm.gm_sketch(rp, ids, w, 16, 1, ws=tiny)
+
+
+def test_estimators_against_oracle():
+    A, B = W.jaccard_pairs(seed=4, n_pairs=40, n_pos=300)
+    k = 256
+    sa, ya, _ = run(gm.gm_sketch, A, k, 11)
+    sb, yb, _ = run(gm.gm_sketch, B, k, 11)
+    dev = "cuda"
+    j = gm.gm_jaccard(torch.from_numpy(sa).to(dev), torch.from_numpy(sb).to(dev)).cpu().numpy()
+    assert np.array_equal(j, oracle.jaccard(sa, sb))
+    c = gm.gm_cardinality(torch.from_numpy(ya).to(dev)).cpu().numpy()
+    c_ref = oracle.cardinality(ya)
+    assert np.allclose(c, c_ref, rtol=k * 2.0 ** -52, atol=0)
+    sm, ym = gm.gm_merge(torch.from_numpy(sa).to(dev), torch.from_numpy(ya).to(dev),
+                         torch.from_numpy(sb).to(dev), torch.from_numpy(yb).to(dev))
+    so, yo = oracle.merge(sa, ya, sb, yb)
+    assert np.array_equal(sm.cpu().numpy(), so) and np.array_equal(ym.cpu().numpy(), yo)
+    # an unfilled register estimates cardinality 0 and never collides
+    y_unf = np.full((1, 8), np.inf)
+    s_unf = np.full((1, 8), -1, np.int32)
+    assert gm.gm_cardinality(torch.from_numpy(y_unf).to(dev)).item() == 0.0
+    assert gm.gm_jaccard(torch.from_numpy(s_unf).to(dev), torch.from_numpy(s_unf).to(dev)).item() == 0.0
+
+
+def test_merge_equals_union_on_gpu():
+    rng = np.random.default_rng(3)
+    ids = np.sort(rng.choice(1 << 20, size=3000, replace=False)).astype(np.int32)
+    wts = rng.standard_exponential(3000)
+    part = rng.random(3000) < 0.4
+    A = W.from_rows([(ids[part], wts[part])])
+    B = W.from_rows([(ids[~part], wts[~part])])
+    U = W.from_rows([(ids, wts)])
+    k = 1024
+    sa, ya, _ = run(gm.gm_sketch, A, k, 5)
+    sb, yb, _ = run(gm.gm_sketch, B, k, 5)
+    su, yu, _ = run(gm.gm_sketch, U, k, 5)
+    dev = "cuda"
+    sm, ym = gm.gm_merge(*(torch.from_numpy(x).to(dev) for x in (sa, ya, sb, yb)))
+    assert np.array_equal(sm.cpu().numpy(), su) and np.array_equal(ym.cpu().numpy(), yu)
+
+
+def test_lognormal_batch_full_size_sampled_rows():
+    """4,096 rows, n+ ~ LogNormal(ln 2000, 1) clipped to [10, 2e5], Exp(1), k = 1024, seed 1:
+    the launch the benchmark times; sampled rows against the oracle, all rows by properties."""
+    X = W.lognormal_batch(seed=1)
+    k, seed = 1024, 1
+    s, y, stats = run(gm.gm_sketch, X, k, seed, flags=0)
+    lens = np.diff(X.row_ptr)
+    order = np.argsort(lens)
+    rng = np.random.default_rng(0)
+    sample = np.unique(np.concatenate([order[:4], rng.choice(np.flatnonzero(lens < 4000), size=6, replace=False)]))
+    s_ref, y_ref, y2_ref = oracle.sketch_rows_parallel(X.row_ptr, X.ids, X.w, k, seed, sample, want_y2=True)
+    rep = compare_sketch(s[sample], y[sample], s_ref, y_ref, y2_ref)
+    assert rep["ok"], rep
+    # properties on every row: all registers filled, ids drawn from the row, times positive
+    assert np.all(np.isfinite(y)) and np.all(y > 0)
+    for r in rng.choice(X.n_rows, size=64, replace=False):
+        assert np.isin(s[r], X.row(r)[0]).all()
