@@ -119,6 +119,37 @@ int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w,
                     void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * gm_sketch_noalloc -- gm_sketch without a workspace argument: it allocates
+ * nothing and takes no scratch from the caller.  (The paper has no counterpart;
+ * this is a library convenience.)
+ *
+ * For callers that cannot allocate device memory or hand the library a
+ * workspace: hosts whose device memory belongs to a framework or plugin
+ * allocator that forbids foreign allocations, serving loops that must never
+ * stall on cudaMalloc (which can synchronise the device and can fail under
+ * memory pressure), and thin foreign-function bindings that can only pass the
+ * input and output buffers.
+ *
+ * The scratch is one fixed device array inside libgm, sized for
+ * nnz <= GM_NOALLOC_MAX_NNZ and k <= GM_MAX_K (about 4.2 MB); every GPU that
+ * loads the library holds it until the process exits.  Arguments and output are
+ * those of gm_sketch (same kernels, same registers), minus the workspace.
+ *   - Returns GM_ENOMEM if nnz > GM_NOALLOC_MAX_NNZ (the fixed scratch is too
+ *     small), GM_EINVAL for GM_FLAG_VALIDATE (a device status could not be read
+ *     back) and for the argument errors of gm_sketch, GM_ECUDA on a CUDA error.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current and caches it; make that
+ *     first call before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents (each
+ *     call first resets what must start at zero).  Calls whose work overlaps on
+ *     the GPU -- on different streams, or from different host threads without
+ *     ordering -- race on it and give undefined registers: order them.
+ */
+#define GM_NOALLOC_MAX_NNZ (1 << 20)
+int gm_sketch_noalloc(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
+                      int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* stream);
+
+/*
  * gm_status -- wait for the work queued on `stream`, then copy the device
  * status and counters of the last call that used `workspace` into *stats
  * (host pointer, may be NULL) and return the device status (GM_OK, GM_EDATA

@@ -530,3 +530,66 @@ extern "C" int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const
   return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags & GM_FLAG_VALIDATE, s_out, y_out,
                            workspace, workspace_bytes, (cudaStream_t)stream, true);
 }
+
+// ---------------------------------------------------------------------------
+// gm_sketch_noalloc: gm_sketch with its scratch in a fixed device array.
+//
+// Some callers cannot give the library a workspace: code whose device memory
+// is owned by a host framework or plugin allocator that forbids foreign
+// allocations, serving loops that must never stall on cudaMalloc (it can
+// synchronise the device and can fail under memory pressure), and thin
+// foreign-function bindings that can only hand over input and output buffers.
+// This entry point serves them: it launches the same kernels as gm_sketch, but
+// the scratch lives in g_noalloc_scratch below, a file-scope device array that
+// every GPU loading the library holds until the process exits.
+//
+// In host code `g_noalloc_scratch` is only a host-side stand-in for the symbol,
+// not a device address, so its device address is looked up with
+// cudaGetSymbolAddress once per device (with that device current) and cached.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace gm {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES =
+    WS_HEADER_BYTES + ((size_t)GM_MAX_K * 8 + 255) / 256 * 256 + ((size_t)GM_NOALLOC_MAX_NNZ * 4 + 255) / 256 * 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+static std::mutex g_noalloc_mutex;
+
+// Device address of g_noalloc_scratch on the current device (looked up once).
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return GM_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GM_ECUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GM_OK;
+}
+
+}  // namespace gm
+
+extern "C" int gm_sketch_noalloc(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
+                                 int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out,
+                                 double* y_out, void* stream) {
+  if (nnz > GM_NOALLOC_MAX_NNZ) return GM_ENOMEM;  // the fixed scratch is too small for this input
+  if (flags & GM_FLAG_VALIDATE) return GM_EINVAL;  // no way to read a device status back
+  const size_t need = gm_sketch_workspace_bytes(n_rows, nnz, k, flags);
+  if (need == 0) return GM_EINVAL;
+  if (need > gm::NOALLOC_SCRATCH_BYTES) return GM_ENOMEM;
+  void* scratch = nullptr;
+  const int rc = gm::noalloc_scratch(&scratch);
+  if (rc != GM_OK) return rc;
+  // The first kernel of every call zeroes the scratch header (status, row counter,
+  // counters) and rewrites the 1/(k-z) table; the heavy list is written before it
+  // is read.  No other state carries over from the previous call.
+  return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags, s_out, y_out, scratch,
+                           gm::NOALLOC_SCRATCH_BYTES, (cudaStream_t)stream, false);
+}

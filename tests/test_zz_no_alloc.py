@@ -1,0 +1,79 @@
+"""gm_sketch_noalloc: the entry point for callers that cannot allocate device memory.
+
+Some callers cannot give the library a workspace (their device memory belongs
+to a framework allocator, or they must never stall on cudaMalloc, or their
+binding can only pass input and output buffers).  gm_sketch_noalloc keeps its
+scratch in a fixed device array inside libgm instead.  This test calls it through
+the C-ABI, twice in a row on different inputs, and checks each result against
+gm_sketch on the same input, within the tolerance the other GPU tests use.  It
+builds its own inputs so it passes alone in a fresh process as well as after the
+rest of the suite.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_05176_gb300 import build as libbuild
+from paper_2302_05176_gb300 import gm
+from paper_2302_05176_gb300 import workloads as W
+from paper_2302_05176_gb300.parity import compare_sketch
+
+pytestmark = pytest.mark.gpu
+
+GM_NOALLOC_MAX_NNZ = 1 << 20
+
+
+@pytest.fixture(scope="module")
+def noalloc():
+    lib = ctypes.CDLL(libbuild.build())
+    f = lib.gm_sketch_noalloc
+    vp = ctypes.c_void_p
+    f.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32,
+                  vp, vp, vp]
+    f.restype = ctypes.c_int
+    return f
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _run_noalloc(fn, X, k, seed):
+    rp, ids, w = gm.to_device(X)
+    s = torch.full((X.n_rows, k), -7, dtype=torch.int32, device="cuda")
+    y = torch.full((X.n_rows, k), -7.0, dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = fn(_p(rp), _p(ids), _p(w), X.n_rows, X.nnz, k, seed, 0, _p(s), _p(y), stream)
+    assert rc == 0, gm.strerror(rc)
+    torch.cuda.synchronize()
+    return s.cpu().numpy(), y.cpu().numpy()
+
+
+def _run_reference(X, k, seed):
+    rp, ids, w = gm.to_device(X)
+    s, y, ws = gm.gm_sketch(rp, ids, w, k, seed)
+    assert gm.gm_status(ws)[0] == gm.GM_OK
+    return s.cpu().numpy(), y.cpu().numpy()
+
+
+def test_noalloc_matches_gm_sketch_twice(noalloc):
+    torch.cuda.set_device(0)
+    cases = [(W.lognormal_batch(seed=21, n_rows=48, median=500.0, hi=6000), 1024, 7),
+             (W.uniform_rows(seed=22, n_rows=9, n_pos=[0, 1, 40, 300, 2500, 7, 64, 1000, 3]), 256, 8)]
+    for X, k, seed in cases:  # two calls in a row through the shared scratch
+        s, y = _run_noalloc(noalloc, X, k, seed)
+        s_ref, y_ref = _run_reference(X, k, seed)
+        rep = compare_sketch(s, y, s_ref, y_ref)
+        assert rep["ok"], rep
+        assert np.array_equal(s, s_ref)  # same kernels: identical registers
+
+
+def test_noalloc_rejects_inputs_beyond_its_scratch(noalloc):
+    # rejected on the host before any launch, so the pointers are never touched
+    fake = ctypes.c_void_p(0x1000)
+    rc = noalloc(fake, fake, fake, 1, GM_NOALLOC_MAX_NNZ + 1, 64, 1, 0, fake, fake, None)
+    assert rc == gm.GM_ENOMEM
+    rc = noalloc(fake, fake, fake, 1, 10, gm.GM_MAX_K + 1, 1, 0, fake, fake, None)
+    assert rc == gm.GM_EINVAL
