@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU-oracle sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", default="all", choices=["all", "fastgm"],
-                    help="fastgm: time only the k=1024 FastGM step (the case profiled with ncu)")
+                    help="fastgm: time only the FastGM step (the case profiled with ncu)")
+    ap.add_argument("--k", type=int, default=K_MAIN, help="k of the --only fastgm step")
+    ap.add_argument("--arith", action="store_true",
+                    help="time the per-arrival arithmetic: FP64 unit vs integer pipes (diagnostic kernels)")
     return ap.parse_args()
 
 
@@ -143,6 +146,53 @@ def cpu_baseline(X, k, seed, rows_budget_s=15.0, n_rows=0):
                       (rows.size, nnz, k, threads)}
 
 
+def run_arith(args):
+    """Throughput of the FP64 / FP32 FMA units and of the per-arrival operations on
+    the FP64 unit and on the integer pipes (include/gm_diag.h)."""
+    import ctypes
+    import torch
+    from paper_2302_05176_gb300 import build as libbuild
+    L = ctypes.CDLL(libbuild.build())
+    vp = ctypes.c_void_p
+    L.gm_diag_fma.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp]
+    L.gm_diag_neglog.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
+    L.gm_diag_dmul.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
+    L.gm_diag_drcp.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
+    st = vp(torch.cuda.current_stream().cuda_stream)
+    P = lambda t: vp(t.data_ptr())
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def time_ms(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"metric": "arithmetic throughput per GB300", "unit": "ops/s"}
+    blocks, iters = nsm * 8, 4096
+    buf = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    for fp64, name in ((1, "fp64_fma"), (0, "fp32_fma")):
+        it = iters if fp64 else iters * 8
+        ms = time_ms(lambda: L.gm_diag_fma(fp64, blocks, it, P(buf), st))
+        out[name] = 8.0 * it * blocks * 256 / (ms * 1e-3)
+    n = 1 << 24
+    rng = np.random.default_rng(0)
+    x = torch.from_numpy(rng.integers(0, 2**62, size=n, dtype=np.int64)).cuda()
+    a = torch.from_numpy(1.0 + rng.random(n)).cuda()
+    b = torch.from_numpy(1.0 + rng.random(n)).cuda()
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    for fp64, tag in ((1, "fp64_unit"), (0, "integer")):
+        out["neg_log_" + tag] = n / (time_ms(lambda: L.gm_diag_neglog(P(x), n, fp64, P(y), st)) * 1e-3)
+        out["mul_" + tag] = n / (time_ms(lambda: L.gm_diag_dmul(P(a), P(b), n, fp64, P(y), st)) * 1e-3)
+        out["rcp_" + tag] = n / (time_ms(lambda: L.gm_diag_drcp(P(a), n, fp64, P(y), st)) * 1e-3)
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -172,6 +222,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.arith:
+        return run_arith(args)
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -218,15 +270,16 @@ def main():
             raise RuntimeError("device status %s" % gm.strerror(code))
         return ms, st
 
+    if args.only == "fastgm":
+        ms, st = timed(gm.gm_sketch, args.k, args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": world * n_rows / (ms * 1e-3), "unit": "sketches/s",
+                              "ms_per_step": ms, "only": "fastgm k=%d" % args.k, "stats": st}), flush=True)
+        return
     clocks = ClockSampler(local)
     clocks.start()
     ms_main, st_main = timed(gm.gm_sketch, K_MAIN, args.steps, args.warmup)
     clk = clocks.stop()
-    if args.only == "fastgm":
-        if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": world * n_rows / (ms_main * 1e-3), "unit": "sketches/s",
-                              "ms_per_step": ms_main, "only": "fastgm k=1024", "stats": st_main}), flush=True)
-        return
     ms_alt, st_alt = timed(gm.gm_sketch, K_ALT, max(2, args.steps // 3), args.warmup)
     ms_plain, st_plain = timed(gm.gm_sketch_plain, K_MAIN, args.plain_steps, 1)
 
@@ -276,7 +329,7 @@ def main():
         "config": {"workload": WORKLOAD, "rows_per_gpu": n_rows, "nnz_per_gpu": nnz, "k": K_MAIN,
                    "l2": "inputs %.0f MB > 129 MB L2; no flush" % (h2d / 1e6), "parallelism": "rows sharded, dp%d" % world},
         "elements_per_s": world * nnz / (ms_main * 1e-3),
-        "arrivals_per_sketch": st_main["arrivals"] / (n_rows * (args.steps + args.warmup)),
+        "arrivals_per_sketch": st_main["arrivals"] / n_rows,
         "k4096": {"sketches_per_s": world * n_rows / (ms_alt * 1e-3), "ms_per_step": ms_alt,
                   "elements_per_s": world * nnz / (ms_alt * 1e-3)},
         "plain_k1024": {"sketches_per_s": world * n_rows / (ms_plain * 1e-3), "ms_per_step": ms_plain,

@@ -62,6 +62,15 @@ extern "C" {
  * == nnz, ids >= 0, weights finite and >= 0.  A violation sets GM_EDATA in the
  * device status (gm_status); the registers of an invalid row are unspecified. */
 #define GM_FLAG_VALIDATE (1u << 0)
+/* Compute -ln(u), the products and 1/v on the FP64 unit (CUDA's log, IEEE
+ * multiply and reciprocal) instead of the default exact integer-pipe arithmetic.
+ * Products and reciprocals are bit-identical either way; the two logarithms
+ * differ by at most one ulp.  Slower on GB300; kept for comparison. */
+#define GM_FLAG_FP64_UNIT (1u << 2)
+/* Testing aid: divide the closed-form bounds of the first pass (and of long-row
+ * chunks) by 8, so that most rows find a register unfilled and take the
+ * escalation paths.  The registers are the same; only the work grows. */
+#define GM_FLAG_TIGHT_BOUND (1u << 3)
 /* Initial pruning bound per row (Sec. 2.2 FastSearch / FastPrune).  Any bound
  * gives the same registers; it only changes how many arrivals are generated. */
 #define GM_BOUND_CLOSED (0u << 4)  /* closed-form quantile of y* (default)          */
@@ -71,12 +80,17 @@ extern "C" {
 
 /* ---- device-side counters, read back by gm_status ------------------------- */
 typedef struct gm_stats {
-  uint64_t arrivals;        /* arrivals generated (light + heavy paths)               */
+  uint64_t arrivals;        /* arrivals generated (light lanes and warp segments)      */
   uint64_t elements;        /* positive elements visited                               */
   uint64_t screened_out;    /* elements whose first arrival exceeded the row bound      */
-  uint64_t heavy_elements;  /* elements streamed by the warp-cooperative path          */
+  uint64_t heavy_elements;  /* elements streamed by 8- or 32-lane segments             */
   uint64_t rows_escalated;  /* row passes repeated with a larger bound (unfilled rows) */
   uint64_t cas_retries;     /* register compare-and-swap retries                        */
+  /* per-warp clock cycles summed over the warps of the sketch kernel: light lanes,
+   * 8-lane segments, 32-lane warps, dense permutations, waiting at barriers, row
+   * setup (sums, bounds), row finish (filled check, output), total */
+  uint64_t cycles_light, cycles_medium, cycles_heavy, cycles_dense, cycles_wait, cycles_setup, cycles_finish,
+      cycles_total;
   uint32_t status;          /* GM_OK, GM_EDATA or GM_ETIMEOUT                           */
   uint32_t reserved;
 } gm_stats;
@@ -112,7 +126,7 @@ int gm_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32
  * gm_sketch_plain -- the straightforward O(k n+) sketch (Sec. 1, "the
  * straightforward method"): every positive element generates all k arrivals.
  * Same arguments, same output as gm_sketch; it exists as the baseline FastGM
- * is measured against.  `flags` accepts GM_FLAG_VALIDATE only.
+ * is measured against.  `flags` accepts GM_FLAG_VALIDATE and GM_FLAG_FP64_UNIT.
  */
 int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
                     int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out,
@@ -131,12 +145,15 @@ int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w,
  * input and output buffers.
  *
  * The scratch is one fixed device array inside libgm, sized for
- * nnz <= GM_NOALLOC_MAX_NNZ and k <= GM_MAX_K (about 4.2 MB); every GPU that
- * loads the library holds it until the process exits.  Arguments and output are
- * those of gm_sketch (same kernels, same registers), minus the workspace.
- *   - Returns GM_ENOMEM if nnz > GM_NOALLOC_MAX_NNZ (the fixed scratch is too
- *     small), GM_EINVAL for GM_FLAG_VALIDATE (a device status could not be read
- *     back) and for the argument errors of gm_sketch, GM_ECUDA on a CUDA error.
+ * nnz <= GM_NOALLOC_MAX_NNZ, n_rows <= GM_NOALLOC_MAX_ROWS and k <= GM_MAX_K
+ * (about 6.3 MB); every GPU that loads the library holds it until the process
+ * exits.  Arguments and output are those of gm_sketch (same kernels, same
+ * registers), minus the workspace.
+ *   - Returns GM_ENOMEM if nnz > GM_NOALLOC_MAX_NNZ or the input needs more
+ *     scratch than the fixed array holds (always fits: n_rows <=
+ *     GM_NOALLOC_MAX_ROWS), GM_EINVAL for GM_FLAG_VALIDATE (a device status could
+ *     not be read back) and for the argument errors of gm_sketch, GM_ECUDA on a
+ *     CUDA error.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current and caches it; make that
  *     first call before any stream capture.
@@ -146,6 +163,7 @@ int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w,
  *     ordering -- race on it and give undefined registers: order them.
  */
 #define GM_NOALLOC_MAX_NNZ (1 << 20)
+#define GM_NOALLOC_MAX_ROWS (1 << 16)
 int gm_sketch_noalloc(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
                       int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* stream);
 

@@ -4,9 +4,9 @@ Method: table-driven logarithm (P. T. P. Tang, "Table-driven implementation of
 the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16(4), 1990),
 carried out in 64/128-bit integer fixed point instead of floating point:
 
-    f in [1, 2),  j = top 7 fraction bits of f,  F_j = 1 + (j + 1/2)/128
+    f in [1, 2),  j = top 8 fraction bits of f,  F_j = 1 + (j + 1/2)/256
     INV_j = RN(2^64 / F_j)                       (u64; 1/F_j to 64 bits)
-    1 + r = f * INV_j / 2^64                      (exact 128-bit product, |r| < 2^-8)
+    1 + r = f * INV_j / 2^64                      (exact 128-bit product, |r| < 2^-9)
     ln f  = ln(1 + r) - ln(INV_j / 2^64)          (an identity: no error from INV_j)
 
 LNF_j = -ln(INV_j / 2^64) is tabulated to 2^-120 from the exact INV_j, so the only
@@ -18,7 +18,7 @@ Run: python gen_log_tables.py > gm_log_tables.h
 import mpmath
 
 mpmath.mp.prec = 200
-TAB_BITS = 7
+TAB_BITS = 8
 N = 1 << TAB_BITS
 
 
@@ -48,6 +48,7 @@ def main():
     ln2 = rn(mpmath.log(2) * mpmath.mpf(2) ** 120)
 
     def arr(name, vals):
+        # indexed per lane: global memory, read through the read-only cache
         out.append("__device__ const uint64_t %s[%d] = {" % (name, len(vals)))
         for i in range(0, len(vals), 4):
             out.append("    " + ", ".join("0x%016xull" % v for v in vals[i:i + 4]) + ",")
@@ -58,14 +59,16 @@ def main():
     arr("LOG_LNF_LO", lnf_lo)
     out.append("constexpr uint64_t LN2_120_HI = 0x%016xull;  // ln 2 * 2^120, rounded" % (ln2 >> 64))
     out.append("constexpr uint64_t LN2_120_LO = 0x%016xull;" % (ln2 & (2 ** 64 - 1)))
-    # ln(1+r) = r - r^2 Q(r),  Q(r) = sum_{i>=2} (-r)^(i-2) / i ; coefficients 1/i at scale 2^62
-    q = [rn(mpmath.mpf(2) ** 62 / i) for i in range(2, 10)]
-    out.append("// 1/i * 2^62 for i = 2..9: the series Q(r) = 1/2 - r/3 + r^2/4 - ... - r^7/9")
-    out.append("constexpr int64_t LOG_Q[8] = {" + ", ".join("%dll" % v for v in q) + "};")
+    # ln(1+r) = r - r^2/2 + r^3 B(r),  B = 1/3 - r/4 + r^2 (1/5 - r/6 + r^2/7)
+    out.append("// (lane-uniform constants) ln(1+r) = r - r^2/2 + r^3 (1/3 - r/4 + r^2 (1/5 - r/6 + r^2/7))")
+    out.append("constexpr int64_t LOG_C3 = %dll;  // 2^62 / 3" % rn(mpmath.mpf(2) ** 62 / 3))
+    out.append("constexpr int32_t LOG_C5 = %d;  // 2^31 / 5" % rn(mpmath.mpf(2) ** 31 / 5))
+    out.append("constexpr int32_t LOG_C6 = %d;  // 2^31 / 6" % rn(mpmath.mpf(2) ** 31 / 6))
+    out.append("constexpr int32_t LOG_C7 = %d;  // 2^31 / 7" % rn(mpmath.mpf(2) ** 31 / 7))
     # -ln(1-w) = w P(w), P(w) = sum_{i>=0} w^i/(i+1) ; coefficients at scale 2^63
     p = [rn(mpmath.mpf(2) ** 63 / (i + 1)) for i in range(9)]
     out.append("// 2^63 / (i+1) for i = 0..8: P(w) = 1 + w/2 + ... + w^8/9 of -ln(1-w) = w P(w)")
-    out.append("constexpr uint64_t LOG1M_P[9] = {" + ", ".join("0x%016xull" % v for v in p) + "};")
+    out.append("__device__ __constant__ uint64_t LOG1M_P[9] = {" + ", ".join("0x%016xull" % v for v in p) + "};")
     out.append("}  // namespace gm")
     print("\n".join(out))
 

@@ -21,6 +21,14 @@ extern "C" int gm_status(const void* workspace, gm_stats* stats, void* stream) {
     stats->heavy_elements = h.counters[3];
     stats->rows_escalated = h.counters[4];
     stats->cas_retries = h.counters[5];
+    stats->cycles_light = h.counters[6];
+    stats->cycles_medium = h.counters[7];
+    stats->cycles_heavy = h.counters[8];
+    stats->cycles_dense = h.counters[9];
+    stats->cycles_wait = h.counters[10];
+    stats->cycles_setup = h.counters[11];
+    stats->cycles_finish = h.counters[12];
+    stats->cycles_total = h.counters[13];
     stats->status = (uint32_t)code;
   }
   return code;

@@ -5,13 +5,15 @@
 //   u   = (2m + 1) 2^-53 from the top 52 bits of Philox words 0,1
 //   E   = RN(-ln u)
 //   t_z = RN(E * C_z),   C_z = RN(1 / (k - z))
-//   S_z = RN(exact sum of t_0..t_z)     -- a 192-bit fixed-point accumulator
+//   S_z = RN(exact sum of t_0..t_z)     -- a 128-bit fixed-point accumulator
 //   b_z = RN(S_z * R),   R = RN(1 / v)
 // The exact sum makes S_z independent of the order in which the terms are
 // added, so a warp can form 32 consecutive prefix sums with a shuffle scan and
 // get the same bits as a sequential loop.
 #pragma once
 #include <cstdint>
+
+#include "gm.h"
 
 namespace gm {
 
@@ -64,64 +66,61 @@ __device__ __forceinline__ int randint(uint32_t w2, uint32_t w3, int z, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// 192-bit unsigned fixed point, value = w0 2^-128 + w1 2^-64 + w2.
-// Every term t_z lies in [2^-70, 2^6) (E >= 2^-53, C >= 2^-12 for k <= 4096), so
-// its lowest mantissa bit is >= 2^-122 and any prefix sum is held exactly.
+// 128-bit unsigned fixed point, value = w0 2^-118 + w1 2^-54.
+// For k <= 4096 every term t_z = RN(E C_z) lies in [2^-65, 2^6) (E >= 2^-53,
+// E <= 53 ln 2 < 36.74, C_z >= 2^-12), so its lowest mantissa bit is >= 2^-117,
+// and every prefix sum is below 36.74 H_4096 < 327 < 2^9: the 128 bits hold each
+// prefix sum exactly.
 // ---------------------------------------------------------------------------
+static_assert(GM_MAX_K <= 4096, "the 128-bit prefix-sum accumulator is exact only for k <= 4096");
+
 struct Fix {
-  uint64_t w0, w1, w2;
+  uint64_t w0, w1;
 };
 
-__device__ __forceinline__ Fix fix_zero() { return Fix{0ull, 0ull, 0ull}; }
+__device__ __forceinline__ Fix fix_zero() { return Fix{0ull, 0ull}; }
 
-// Exact conversion of a positive normal double in [2^-76, 2^52).
+// Exact conversion of a positive normal double in [2^-65, 2^10).
 __device__ __forceinline__ Fix fix_from(double t) {
   const uint64_t bits = (uint64_t)__double_as_longlong(t);
   const int e = (int)(bits >> 52);
   const uint64_t M = (bits & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
-  const int off = e - 947;  // bit index of M's lowest bit: (e - 1075) + 128
+  const int off = e - 957;  // bit index of M's lowest bit: (e - 1075) + 118, >= 1
   Fix f;
   if (off < 64) {
     f.w0 = M << off;
-    f.w1 = (off > 11) ? (M >> (64 - off)) : 0ull;
-    f.w2 = 0ull;
+    f.w1 = M >> (64 - off);
   } else {
-    const int o = off - 64;
     f.w0 = 0ull;
-    f.w1 = M << o;
-    f.w2 = (o > 11) ? (M >> (64 - o)) : 0ull;
+    f.w1 = M << (off - 64);
   }
   return f;
 }
 
 __device__ __forceinline__ void fix_add(Fix& a, const Fix& b) {
-  asm("add.cc.u64 %0, %0, %3;\n\t"
-      "addc.cc.u64 %1, %1, %4;\n\t"
-      "addc.u64 %2, %2, %5;"
-      : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2)
-      : "l"(b.w0), "l"(b.w1), "l"(b.w2));
+  asm("add.cc.u64 %0, %0, %2;\n\t"
+      "addc.u64 %1, %1, %3;"
+      : "+l"(a.w0), "+l"(a.w1)
+      : "l"(b.w0), "l"(b.w1));
 }
 
-// Round a positive fixed-point value (>= 2^-76) to the nearest double, ties to even.
+// Round a positive fixed-point value (>= 2^-65) to the nearest double, ties to even.
 __device__ __forceinline__ double fix_round(const Fix& a) {
   uint64_t hi, lo;
-  bool rest;
   int base;
-  if (a.w2) {
-    hi = a.w2; lo = a.w1; rest = (a.w0 != 0ull); base = 128;
-  } else if (a.w1) {
-    hi = a.w1; lo = a.w0; rest = false; base = 64;
+  if (a.w1) {
+    hi = a.w1; lo = a.w0; base = 64;
   } else {
-    hi = a.w0; lo = 0ull; rest = false; base = 0;
+    hi = a.w0; lo = 0ull; base = 0;
   }
   const int s = __clzll((long long)hi);
   const uint64_t H = s ? ((hi << s) | (lo >> (64 - s))) : hi;
   const uint64_t L = lo << s;
-  const int p = base + 63 - s;  // index of the leading one, in units of 2^-128
+  const int p = base + 63 - s;  // index of the leading one, in units of 2^-118
   const uint64_t mant = H >> 11;
   const uint64_t rbit = (H >> 10) & 1ull;
-  const bool sticky = ((H & 0x3FFull) != 0ull) || (L != 0ull) || rest;
-  uint64_t bits = ((uint64_t)(p + 894) << 52) + mant;  // mant carries the implicit one
+  const bool sticky = ((H & 0x3FFull) != 0ull) || (L != 0ull);
+  uint64_t bits = ((uint64_t)(p + 904) << 52) + mant;  // mant carries the implicit one
   bits += (rbit && (sticky || (mant & 1ull))) ? 1ull : 0ull;
   return __longlong_as_double((long long)bits);
 }

@@ -7,50 +7,90 @@
 
 namespace gm {
 
-constexpr int WS_NCOUNTERS = 6;  // arrivals, elements, screened, heavy, escalated, cas retries
+// arrivals, elements, screened, warp-path elements, escalated passes, CAS retries, then the
+// summed per-warp clocks of the light, 8-lane, 32-lane, dense phases, barrier waits, row setup,
+// row finish and the total
+constexpr int WS_NCOUNTERS = 14;
 constexpr uint32_t WS_EDATA = 1u;
 constexpr uint32_t WS_ETIMEOUT = 2u;
+constexpr int SPLIT_LEN = 32768;  // rows longer than this are cut into chunks of this many elements
 
 // Start of every workspace; zeroed by the first kernel of each call.
 struct WsHeader {
-  uint32_t status;       // WS_* bits
-  uint32_t row_counter;  // next row for the persistent grid
+  uint32_t status;        // WS_* bits
+  uint32_t unit_counter;  // next work unit of the persistent grid
+  uint32_t n_long;        // rows longer than SPLIT_LEN
+  uint32_t n_extra;       // chunk units of long rows beyond their first chunk
+  uint32_t esc_count;     // long rows to redo with a larger bound
+  uint32_t esc_counter;   // next entry of that list
   uint32_t pad[2];
   unsigned long long counters[WS_NCOUNTERS];
 };
 
+// Per long row: its row index, chunk count, first extra unit, sum of weights.
+struct LongRow {
+  uint32_t row;
+  uint32_t nchunks;
+  uint32_t chunk_off;  // index of its first extra unit (chunks 1 .. nchunks-1)
+  uint32_t done;       // chunks finished
+  float sum;           // sum of positive weights (FP32, places the bound only)
+  int npos;            // positive weights
+  uint32_t pad[2];
+};
+
 constexpr size_t WS_HEADER_BYTES = 256;
 
-inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+constexpr size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Workspace: header | C table (k doubles) | heavy list (nnz u32)
+constexpr int64_t max_long_rows(int64_t nnz) { return nnz / (SPLIT_LEN + 1) + 1; }
+
+// Workspace: header | C table (k doubles) | work list (nnz u32) | promotion list
+// (nnz u32) | long index per row (n_rows i32) | long rows (max_long) | long
+// registers (max_long * k * 16 B) | escalation list (max_long u32)
 struct WsLayout {
   WsHeader* hdr;
   double* ctab;
-  uint32_t* heavy;
+  uint32_t* list;
+  uint32_t* plist;
+  int32_t* long_idx;
+  LongRow* longs;
+  void* long_regs;
+  uint32_t* esc;
+  int64_t max_long;
 };
 
-inline size_t ws_bytes(int64_t nnz, int k) {
-  return WS_HEADER_BYTES + round_up((size_t)k * 8, 256) + round_up((size_t)nnz * 4, 256);
-}
-
-inline WsLayout ws_layout(void* ws, int64_t nnz, int k) {
-  (void)nnz;
+inline WsLayout ws_layout(void* ws, int32_t n_rows, int64_t nnz, int k) {
   unsigned char* p = static_cast<unsigned char*>(ws);
   WsLayout L;
-  L.hdr = reinterpret_cast<WsHeader*>(p);
-  L.ctab = reinterpret_cast<double*>(p + WS_HEADER_BYTES);
-  L.heavy = reinterpret_cast<uint32_t*>(p + WS_HEADER_BYTES + round_up((size_t)k * 8, 256));
+  const int64_t ml = max_long_rows(nnz);
+  size_t off = 0;
+  L.hdr = reinterpret_cast<WsHeader*>(p + off);
+  off += WS_HEADER_BYTES;
+  L.ctab = reinterpret_cast<double*>(p + off);
+  off += round_up((size_t)k * 8, 256);
+  L.list = reinterpret_cast<uint32_t*>(p + off);
+  off += round_up((size_t)nnz * 4, 256);
+  L.plist = reinterpret_cast<uint32_t*>(p + off);
+  off += round_up((size_t)nnz * 4, 256);
+  L.long_idx = reinterpret_cast<int32_t*>(p + off);
+  off += round_up((size_t)n_rows * 4, 256);
+  L.longs = reinterpret_cast<LongRow*>(p + off);
+  off += round_up((size_t)ml * sizeof(LongRow), 256);
+  L.long_regs = p + off;
+  off += round_up((size_t)ml * (size_t)k * 16, 256);
+  L.esc = reinterpret_cast<uint32_t*>(p + off);
+  L.max_long = ml;
   return L;
 }
 
-// Shared memory of the sketch kernel besides the registers: the light lanes'
-// sparse maps (32 entries x 256 lanes x 4 B) or, reusing the same bytes, the
-// warps' dense permutations (8 warps x k x 2 B).
-__host__ __device__ inline size_t area_size_bytes(int k) {
-  size_t a = (size_t)32 * 256 * 4, b = (size_t)8 * (size_t)k * 2;
-  size_t m = a > b ? a : b;
-  return (m + 15) / 16 * 16;
+constexpr size_t ws_bytes(int32_t n_rows, int64_t nnz, int k) {
+  return WS_HEADER_BYTES + round_up((size_t)k * 8, 256) + 2 * round_up((size_t)nnz * 4, 256) +
+         round_up((size_t)n_rows * 4, 256) + round_up((size_t)max_long_rows(nnz) * sizeof(LongRow), 256) +
+         round_up((size_t)max_long_rows(nnz) * (size_t)k * 16, 256) + round_up((size_t)max_long_rows(nnz) * 4, 256);
 }
+
+// Entries per dense permutation: k rounded up to a multiple of 8, so that each
+// array starts on a 16-byte boundary (16-byte stores).
+__host__ __device__ inline size_t pi_stride(int k) { return ((size_t)k + 7) / 8 * 8; }
 
 }  // namespace gm

@@ -1,30 +1,34 @@
 // gm_sketch.cu -- FastGM (Algorithm 1, Sec. 2.2) and the plain O(k n+) sketch on GB300.
 //
-// One CTA sketches one row at a time (persistent grid, rows taken from a global
-// counter).  The k registers live in shared memory as 16-byte (y, id) pairs.
+// Work is cut into units: one per row, plus one per extra chunk of SPLIT_LEN
+// elements of a long row.  A persistent grid of 512-thread CTAs takes units from
+// a counter (long-row chunks first).  The k registers of a unit live in shared
+// memory as 16-byte (y, id) pairs lowered by 128-bit compare-and-swap; the units
+// of a long row then merge their registers into global memory with the same
+// compare-and-swap, the union of Sec. 2.3 (Mergeability), and the last one writes
+// the row.
 //
-// FastGM, per row:
-//   1. sum v over the row (FP32, only used to place the bound) and the bound
-//      T = q(p) / sum v, where q(p) is the (1-p) quantile of y* sum v, whose law
-//      (1 - e^-t)^k is the one derived in Sec. 2.3 (Time Complexity).  T plays
-//      the role of FastSearch's release horizon R/(k sum v) (Eq. exiri): every
-//      arrival <= T is generated, nothing above it.
-//   2. light path: every lane owns one element at a time and walks its
-//      ascending arrival stream (Eq. biz_biz-1) until an arrival exceeds T
-//      (FastPrune's stopping rule); when its element is done it takes the next
-//      one from the row's pool, so lanes stay busy while streams differ in
-//      length.  The Fisher-Yates state is a small per-lane map of displaced
-//      positions in shared memory.
-//   3. heavy path: elements expected to need many arrivals (or whose map
-//      overflowed) are streamed by a whole warp, 32 arrivals per step, with a
-//      dense permutation in shared memory and an exact shuffle scan of the
-//      prefix sums.
-//   4. if a register is still empty, no arrival <= T reached it: T is raised
-//      and the row is redone (registers keep their values; every update is an
-//      idempotent minimum).  Once every register holds an arrival <= T, each
-//      holds the minimum over ALL arrivals: the result equals the full stream.
-// The plain sketch runs every positive element through the heavy path with no
-// bound, i.e. all k arrivals of every element (Sec. 1, straightforward method).
+// FastGM, per unit:
+//   1. a bound T = q(p) / sum v, q(p) the (1-p) quantile of y* sum v, whose law
+//      (1 - e^-t)^k is the one of Sec. 2.3 (Time Complexity).  T plays the role
+//      of FastSearch's release horizon R/(k sum v) (Eq. exiri): every arrival
+//      <= T is generated, nothing above it.
+//   2. warp screening: a warp takes 32 elements, sorts out those whose first
+//      arrival is certainly above T (an FP32 test, no FP64 work), those expected
+//      to need many arrivals (to the warp path) and the rest, which it hands to
+//      its idle lanes.
+//   3. light path: every lane walks its own element's ascending arrival stream
+//      (Eq. biz_biz-1) until an arrival exceeds T (FastPrune's stopping rule),
+//      the Fisher-Yates state a per-lane map of displaced positions.
+//   4. warp path: 32 arrivals per step, exact shuffle scan of the prefix sums,
+//      parallel Fisher-Yates on a per-warp hash of displaced positions; streams
+//      too long for the hash go to one dense permutation per CTA.
+//   5. if a register is still empty, no arrival <= T reached it: T is raised and
+//      the row is redone (updates are idempotent minima).  Once every register
+//      holds an arrival <= T, each holds the minimum over ALL arrivals, so the
+//      result equals the full stream whatever T was.
+// The plain sketch runs every positive element through the warp path with no
+// bound: all k arrivals of every element (Sec. 1, the straightforward method).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -33,18 +37,29 @@
 #include "gm.h"
 #include "gm_device.cuh"
 #include "gm_internal.h"
+#include "gm_stream.cuh"
 
 namespace gm {
 
-constexpr int BLOCK = 256;
+constexpr int BLOCK = 512;
 constexpr int WARPS = BLOCK / 32;
-constexpr int MAPCAP = 32;             // displaced positions a light lane can track
-constexpr float HEAVY_EXPECT = 16.0f;  // expected arrivals above which an element goes to a warp
+constexpr int MAPCAP = 16;              // displaced positions a light lane can track
+constexpr float LIGHT_MAX = 6.0f;       // expected arrivals <= T: light lane path up to this,
+constexpr float MEDIUM_MAX = 48.0f;     //   8-lane segments up to this,
+constexpr float HEAVY_MAX = 256.0f;     //   32-lane warps up to this, dense permutation beyond
+constexpr int MED_SW = 8;
+constexpr int MED_SLOTS = 128;          // hash slots per 8-lane segment
+constexpr int MED_MAX_FILL = 96;        // beyond: the element moves to a 32-lane warp
+constexpr uint32_t TAG_MEDIUM = 1u << 30, TAG_HEAVY = 2u << 30, TAG_SUPER = 3u << 30;
+constexpr uint32_t TAG_MASK = 3u << 30, SLOT_MASK = (1u << 30) - 1u;
 
+// Per-thread counters (the per-warp phase clocks live in shared memory).
 struct Counters {
-  unsigned long long arrivals, elements, screened, heavy, escalated, cas;
-  __device__ void zero() { arrivals = elements = screened = heavy = escalated = cas = 0ull; }
+  uint32_t arrivals, elements, screened, heavy, escalated, cas;
+  __device__ void zero() { arrivals = elements = screened = heavy = escalated = cas = 0u; }
 };
+constexpr int CLK_LIGHT = 0, CLK_MEDIUM = 1, CLK_HEAVY = 2, CLK_SUPER = 3, CLK_WAIT = 4, CLK_SETUP = 5,
+              CLK_FINISH = 6, CLK_TOTAL = 7, NCLK = 8;
 
 struct SketchArgs {
   const int64_t* row_ptr;
@@ -59,73 +74,39 @@ struct SketchArgs {
   double* y_out;
   WsHeader* hdr;
   const double* ctab;
-  uint32_t* heavy;
-  float q1, q2;  // normalised bounds of the first two passes (inf = no bound)
+  uint32_t* list;   // work list of the unit's warp-path elements, at the unit's element range
+  uint32_t* plist;  // elements promoted from 8-lane segments to warps, same ranges
+  int32_t* long_idx;
+  LongRow* longs;
+  Reg* long_regs;
+  uint32_t* esc;
+  int max_long;
+  int ndense;             // dense permutations per CTA (warps that take super-heavy elements)
+  float q1, q2, q_split;  // normalised bounds: first pass, later passes, long rows (inf = none)
 };
 
 struct SmemScalars {
-  int pool, hcount, hnext, row;
+  int pool, hcount, pcount, c_med, c_heavy, c_pheavy, c_super, c_psuper, unit, last;
   float red_f[WARPS];
   int red_i[WARPS];
+  unsigned long long clk[WARPS][NCLK];  // light, 8-lane, 32-lane, dense, barrier wait, setup, finish, total
 };
+__shared__ SmemScalars sh_scalars;
 
-// --------------------------------------------------------------------------
-// Warp-cooperative stream of one element: 32 consecutive arrivals per step.
-// --------------------------------------------------------------------------
-__device__ __forceinline__ void heavy_element(int32_t id, double v, int k, uint32_t key0, uint32_t key1,
-                                              uint64_t Tbits, const double* __restrict__ ctab, Reg* regs,
-                                              uint16_t* pi, int* scr, int lane, Counters& cnt,
-                                              bool& gave_up) {
-  const double R = __drcp_rn(v);
-  for (int j = lane; j < k; j += 32) pi[j] = (uint16_t)j;
-  __syncwarp();
-  Fix carry = fix_zero();
-  for (int z0 = 0; z0 < k; z0 += 32) {
-    const int z = z0 + lane;
-    const bool valid = z < k;
-    Fix f = fix_zero();
-    int J = z;
-    if (valid) {
-      const Words wd = philox((uint32_t)id, (uint32_t)z, key0, key1);
-      const double u = uniform_open(wd.w0, wd.w1);
-      const double t = __dmul_rn(-log(u), __ldg(ctab + z));
-      f = fix_from(t);
-      J = randint(wd.w2, wd.w3, z, k);
-    }
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      Fix g;
-      g.w0 = __shfl_up_sync(FULL, f.w0, d);
-      g.w1 = __shfl_up_sync(FULL, f.w1, d);
-      g.w2 = __shfl_up_sync(FULL, f.w2, d);
-      if (lane >= d) fix_add(f, g);
-    }
-    fix_add(f, carry);
-    const double S = fix_round(f);
-    const uint64_t bb = (uint64_t)__double_as_longlong(__dmul_rn(S, R));
-    const bool keep = valid && bb <= Tbits;
-    const uint32_t km = __ballot_sync(FULL, keep);
-    const int nkeep = (km == FULL) ? 32 : (__ffs(~km) - 1);  // arrivals ascend: keep is a prefix
-    if (lane == 0) cnt.arrivals += (unsigned long long)min(32, k - z0);
-    scr[lane] = J;
-    __syncwarp();
-    if (lane == 0) {
-      for (int l = 0; l < nkeep; ++l) {  // Fisher-Yates steps z0 .. z0+nkeep-1, in order
-        const int p = z0 + l, j = scr[l];
-        const uint16_t a = pi[p];
-        const uint16_t c = pi[j];
-        pi[j] = a;
-        scr[l] = c;
-      }
-    }
-    __syncwarp();
-    if (lane < nkeep) cnt.cas += reg_lower(smem_addr(&regs[scr[lane]]), bb, (uint64_t)(uint32_t)id, gave_up);
-    carry.w0 = __shfl_sync(FULL, f.w0, 31);
-    carry.w1 = __shfl_sync(FULL, f.w1, 31);
-    carry.w2 = __shfl_sync(FULL, f.w2, 31);
-    __syncwarp();
-    if (nkeep < 32) break;
-  }
+// Shared memory of the FastGM kernel: registers | light maps, 8-lane hashes or
+// warp hashes | ndense dense permutations | per-warp screening buffers.
+__host__ __device__ inline size_t fast_area_bytes() {
+  const size_t maps = (size_t)MAPCAP * BLOCK * 4, hashes = (size_t)WARPS * HASH_SLOTS * 4;
+  const size_t med = (size_t)WARPS * (32 / MED_SW) * MED_SLOTS * 4;
+  size_t m = maps > hashes ? maps : hashes;
+  return m > med ? m : med;
+}
+__host__ __device__ inline size_t fast_smem_bytes(int k, int ndense) {
+  return (size_t)k * sizeof(Reg) + fast_area_bytes() + (size_t)ndense * pi_stride(k) * 2 + (size_t)WARPS * 32 * 4;
+}
+// The plain kernel: registers | one dense permutation per warp.
+__host__ __device__ inline size_t plain_smem_bytes(int k) {
+  return (size_t)k * sizeof(Reg) + (size_t)WARPS * pi_stride(k) * 2;
 }
 
 __device__ __forceinline__ bool positive_finite(double v) {
@@ -134,11 +115,89 @@ __device__ __forceinline__ bool positive_finite(double v) {
 }
 
 // --------------------------------------------------------------------------
-// Light path: lanes walk their own element's stream, refilling from the pool.
+// Segment path: each SW-lane segment of a warp claims entries of class `want`
+// from a work list and streams them SW arrivals per step until an arrival
+// exceeds T (arrivals ascend).  An element whose permutation outgrows the
+// segment's table is promoted: appended to `promote` (tagged TAG_HEAVY) or,
+// without a promote list, retagged TAG_SUPER in place.  Updates are idempotent,
+// so a promoted element simply starts again from its first arrival.
 // --------------------------------------------------------------------------
+template <int ARITH, int SW, class PI>
+__device__ __forceinline__ void seg_phase(const SketchArgs& a, int64_t lo, uint64_t Tbits, Reg* regs,
+                                          uint32_t* list, int count, int* cursor, uint32_t want, const PI& pi,
+                                          int fill_limit, uint32_t* promote, int* promote_count, Counters& cnt,
+                                          bool& gave_up) {
+  constexpr uint32_t SEGM = SW == 32 ? 0xFFFFFFFFu : ((1u << SW) - 1u);
+  const int lane = threadIdx.x & 31, sl = lane & (SW - 1), base = lane & ~(SW - 1);
+  const int k = a.k;
+  int eidx = -1, z0 = 0, fill = 0;
+  uint32_t entry = 0u;
+  int32_t id = 0;
+  double R = 0.0;
+  Fix carry = fix_zero();
+  bool list_done = false;
+  while (true) {
+    const bool need = (eidx < 0) && !list_done;  // uniform within the segment
+    int h = 0;
+    if (need && sl == 0) h = atomicAdd(cursor, 1);
+    h = __shfl_sync(FULL, h, base);
+    if (need) {
+      if (h >= count) {
+        list_done = true;
+      } else {
+        const uint32_t e = list[h];
+        if ((e & TAG_MASK) == want) {
+          eidx = h;
+          entry = e;
+          const int64_t g = lo + (e & SLOT_MASK);
+          id = a.ids[g];
+          R = arr_rcp<ARITH>(a.w[g]);
+          z0 = 0;
+          fill = 0;
+          carry = fix_zero();
+          pi.reset_seg(k, sl, SW);
+          if (sl == 0) ++cnt.heavy;
+        }
+      }
+    }
+    __syncwarp();
+    const bool act = eidx >= 0;
+    if (!__any_sync(FULL, act || !list_done)) break;
+    if (!__any_sync(FULL, act)) continue;
+    int J;
+    const uint64_t bb = seg_batch<ARITH, SW>(act, id, R, z0, k, a.key0, a.key1, a.ctab, carry, lane, J);
+    const uint32_t field = (__ballot_sync(FULL, bb <= Tbits) >> base) & SEGM;
+    const int nkeep = act ? (field == SEGM ? SW : (__ffs(~field) - 1)) : 0;
+    if (act && sl == 0) cnt.arrivals += (uint32_t)min(SW, k - z0);
+    int c;
+    fill += seg_fy_steps<SW>(pi, z0, J, nkeep, lane, c);
+    if (sl < nkeep) cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
+    z0 += SW;
+    if (act) {
+      if (nkeep < SW || z0 >= k) {
+        eidx = -1;
+      } else if (fill > fill_limit) {  // too long for this table: promote
+        if (sl == 0) {
+          if (promote)
+            promote[atomicAdd(promote_count, 1)] = (entry & SLOT_MASK) | TAG_HEAVY;
+          else
+            list[eidx] = (entry & SLOT_MASK) | TAG_SUPER;
+        }
+        eidx = -1;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Light path with warp screening.  Elements [lo, lo+n) of the unit; T as bits and
+// as an FP32 value (equal as reals).  Elements expected to need more than
+// LIGHT_MAX arrivals go to the work list, tagged by their expected count.
+// --------------------------------------------------------------------------
+template <int ARITH>
 __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int n, uint64_t Tbits, float Tf,
-                                            Reg* regs, uint32_t* map, SmemScalars& sh, Counters& cnt,
-                                            bool& gave_up) {
+                                            Reg* regs, uint32_t* map, uint32_t* wbuf, SmemScalars& sh,
+                                            Counters& cnt, bool& gave_up) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int k = a.k;
   const float kf = (float)k;
@@ -146,51 +205,68 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
   int32_t id = 0;
   double R = 0.0;
   Fix acc = fix_zero();
+  int wcount = 0;
   bool pool_done = false;
   while (true) {
-    const bool need = (e < 0) && !pool_done;
-    const uint32_t nmask = __ballot_sync(FULL, need);
-    if (nmask) {
-      const int leader = __ffs(nmask) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(&sh.pool, __popc(nmask));
-      base = __shfl_sync(FULL, base, leader);
-      if (need) {
-        const int slot = base + __popc(nmask & lanemask_lt());
-        if (slot >= n) {
+    // hand survivors to idle lanes, screening new elements while some are idle
+    uint32_t nmask = __ballot_sync(FULL, e < 0);
+    while (nmask && !(pool_done && wcount == 0)) {
+      if (wcount == 0) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&sh.pool, 32);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= n) {
           pool_done = true;
-        } else {
-          const int64_t g = lo + slot;
-          const double v = a.w[g];
+          break;
+        }
+        const int slot = base + lane;
+        bool surv = false;
+        if (slot < n) {
+          const double v = a.w[lo + slot];
           if (positive_finite(v)) {
             ++cnt.elements;
-            const float lam = kf * (1.0f - __expf(-f32_trunc(v) * Tf));
-            if (lam > HEAVY_EXPECT) {
-              a.heavy[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot;
+            const float vf = f32_trunc(v);
+            const float lam = kf * (1.0f - __expf(-(vf * Tf)));  // expected arrivals <= T (routing only)
+            if (lam > LIGHT_MAX) {
+              const uint32_t tag = lam > HEAVY_MAX ? TAG_SUPER : (lam > MEDIUM_MAX ? TAG_HEAVY : TAG_MEDIUM);
+              a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | tag;
             } else {
-              e = slot;
-              id = a.ids[g];
-              R = __drcp_rn(v);
-              z = 0;
-              acc = fix_zero();
-              msize = 0;
+              const Words wd = philox((uint32_t)a.ids[lo + slot], 0u, a.key0, a.key1);
+              if (screen_out(wd.w1, vf, Tf, kf))
+                ++cnt.screened;  // first arrival certainly above T: nothing of it counts
+              else
+                surv = true;
             }
           }
         }
+        const uint32_t sm = __ballot_sync(FULL, surv);
+        if (surv) wbuf[__popc(sm & lanemask_lt())] = (uint32_t)slot;
+        wcount = __popc(sm);
+        __syncwarp();
+        continue;
       }
+      const int take = min(__popc(nmask), wcount);
+      const int rank = __popc(nmask & lanemask_lt());
+      if (e < 0 && rank < take) {
+        e = (int)wbuf[wcount - 1 - rank];
+        const int64_t g = lo + e;
+        id = a.ids[g];
+        R = arr_rcp<ARITH>(a.w[g]);
+        z = 0;
+        acc = fix_zero();
+        msize = 0;
+      }
+      wcount -= take;
+      __syncwarp();
+      nmask = __ballot_sync(FULL, e < 0);
     }
-    const bool active = e >= 0;
-    if (!__any_sync(FULL, active || !pool_done)) break;
-    if (!active) continue;
+    if (!__any_sync(FULL, e >= 0)) break;  // nothing left to stream
+    if (e < 0) continue;
     const Words wd = philox((uint32_t)id, (uint32_t)z, a.key0, a.key1);
-    const double u = uniform_open(wd.w0, wd.w1);
-    const double t = __dmul_rn(-log(u), __ldg(a.ctab + z));
-    fix_add(acc, fix_from(t));
-    const double S = fix_round(acc);
-    const uint64_t bb = (uint64_t)__double_as_longlong(__dmul_rn(S, R));
+    fix_add(acc, fix_from(arr_mul_t<ARITH>(arr_neglog<ARITH>(wd), __ldg(a.ctab + z))));
+    const uint64_t bb = (uint64_t)__double_as_longlong(arr_mul<ARITH>(fix_round(acc), R));
     ++cnt.arrivals;
     if (bb > Tbits) {  // FastPrune: the rest of this stream is above the bound
-      if (z == 0) ++cnt.screened;
       e = -1;
       continue;
     }
@@ -230,13 +306,78 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
         }
       }
     }
-    if (overflow) {  // restart this element on the warp path (updates are idempotent)
-      a.heavy[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)e;
+    if (overflow) {  // restart this element on an 8-lane segment (updates are idempotent)
+      a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)e | TAG_MEDIUM;
       e = -1;
       continue;
     }
     cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
     if (++z >= k) e = -1;
+  }
+}
+
+// SM clock, ordered with the surrounding memory operations and barriers.
+__device__ __forceinline__ long long read_clock() {
+  long long c;
+  asm volatile("mov.u64 %0, %%clock64;" : "=l"(c) : : "memory");
+  return c;
+}
+
+__device__ __forceinline__ void clk_add(Counters&, int which, long long& t) {
+  const long long now = read_clock();
+  if ((threadIdx.x & 31) == 0) sh_scalars.clk[threadIdx.x >> 5][which] += (unsigned long long)(now - t);
+  t = now;
+}
+
+// All warp-path classes of one pass, in order: 8-lane segments, 32-lane warps
+// (work list, then promotions), dense permutations (warps < ndense).
+template <int ARITH>
+__device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uint64_t Tbits, Reg* regs,
+                                            uint32_t* area, uint16_t* dense, SmemScalars& sh, Counters& cnt,
+                                            bool& gave_up, long long& t) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nh = sh.hcount;
+  {
+    const int seg = lane / MED_SW;
+    const HashPiN<MED_SLOTS> hp{area + (warp * (32 / MED_SW) + seg) * MED_SLOTS};
+    seg_phase<ARITH, MED_SW>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_med, TAG_MEDIUM, hp, MED_MAX_FILL,
+                             a.plist + lo, &sh.pcount, cnt, gave_up);
+  }
+  clk_add(cnt, CLK_MEDIUM, t);
+  __syncthreads();
+  clk_add(cnt, CLK_WAIT, t);
+  {
+    const HashPi hp{area + warp * HASH_SLOTS};
+    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_heavy, TAG_HEAVY, hp, HASH_MAX_FILL, nullptr,
+                         nullptr, cnt, gave_up);
+    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_pheavy, TAG_HEAVY, hp, HASH_MAX_FILL,
+                         nullptr, nullptr, cnt, gave_up);
+  }
+  clk_add(cnt, CLK_HEAVY, t);
+  __syncthreads();
+  clk_add(cnt, CLK_WAIT, t);
+  // dense permutations: the CTA's own, then as many as fit in the (now idle) hash area
+  const int ndense = min(WARPS, a.ndense + (int)(fast_area_bytes() / (pi_stride(a.k) * 2)));
+  if (warp < ndense) {
+    uint16_t* mine = warp < a.ndense ? dense + (size_t)warp * pi_stride(a.k)
+                                     : reinterpret_cast<uint16_t*>(area) + (size_t)(warp - a.ndense) * pi_stride(a.k);
+    const DensePi dp{mine};
+    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_super, TAG_SUPER, dp, 1 << 30, nullptr,
+                         nullptr, cnt, gave_up);
+    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_psuper, TAG_SUPER, dp, 1 << 30,
+                         nullptr, nullptr, cnt, gave_up);
+  }
+  clk_add(cnt, CLK_SUPER, t);
+  __syncthreads();
+  clk_add(cnt, CLK_WAIT, t);
+}
+
+__device__ __forceinline__ void reset_lists(SmemScalars& sh) {
+  if (threadIdx.x == 0) {
+    sh.pool = 0;
+    sh.hcount = 0;
+    sh.pcount = 0;
+    sh.c_med = sh.c_heavy = sh.c_pheavy = sh.c_super = sh.c_psuper = 0;
   }
 }
 
@@ -247,7 +388,7 @@ __device__ __forceinline__ void init_regs(Reg* regs, int k) {
   }
 }
 
-__device__ __forceinline__ void write_row(const SketchArgs& a, int row, const Reg* regs) {
+__device__ __forceinline__ void write_out(const SketchArgs& a, int row, const Reg* regs) {
   const int k = a.k;
   int32_t* s = a.s_out + (int64_t)row * k;
   double* y = a.y_out + (int64_t)row * k;
@@ -268,17 +409,19 @@ __device__ __forceinline__ void row_bounds(const SketchArgs& a, int row, int64_t
   hi = h;
 }
 
-// Sum of the positive weights (FP32, from bits) and the count of positives.
-__device__ __forceinline__ void row_sum(const SketchArgs& a, int64_t lo, int n, SmemScalars& sh, float& sum,
-                                        int& npos) {
+// Sum of the positive weights of [lo, lo+n) (FP32 from bits, Kahan) and their count;
+// validates the elements when asked.  Block-wide; contains __syncthreads.
+template <int NT>
+__device__ __forceinline__ void block_sum(const SketchArgs& a, int64_t lo, int n, float* red_f, int* red_i,
+                                          float& sum, int& npos) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float s = 0.0f, comp = 0.0f;
   int c = 0;
   bool bad = false;
-  for (int i = tid; i < n; i += BLOCK) {
+  for (int i = tid; i < n; i += NT) {
     const double v = a.w[lo + i];
     if (positive_finite(v)) {
-      const float y = f32_trunc(v) - comp;  // Kahan
+      const float y = f32_trunc(v) - comp;
       const float t = s + y;
       comp = (t - s) - y;
       s = t;
@@ -296,15 +439,15 @@ __device__ __forceinline__ void row_sum(const SketchArgs& a, int64_t lo, int n, 
     c += __shfl_xor_sync(FULL, c, d);
   }
   if (lane == 0) {
-    sh.red_f[warp] = s;
-    sh.red_i[warp] = c;
+    red_f[warp] = s;
+    red_i[warp] = c;
   }
   __syncthreads();
   float ts = 0.0f;
   int tc = 0;
-  for (int q = 0; q < WARPS; ++q) {
-    ts += sh.red_f[q];
-    tc += sh.red_i[q];
+  for (int q = 0; q < NT / 32; ++q) {
+    ts += red_f[q];
+    tc += red_i[q];
   }
   sum = ts;
   npos = tc;
@@ -313,112 +456,299 @@ __device__ __forceinline__ void row_sum(const SketchArgs& a, int64_t lo, int n, 
 
 __device__ __forceinline__ void flush_counters(const SketchArgs& a, Counters& cnt, bool gave_up) {
   const int lane = threadIdx.x & 31;
-  unsigned long long v[6] = {cnt.arrivals, cnt.elements, cnt.screened, cnt.heavy, cnt.escalated, cnt.cas};
+  const uint32_t v32[6] = {cnt.arrivals, cnt.elements, cnt.screened, cnt.heavy, cnt.escalated, cnt.cas};
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
+    unsigned long long v = v32[q];
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v[q] += __shfl_xor_sync(FULL, v[q], d);
-    if (lane == 0 && v[q]) atomicAdd(&a.hdr->counters[q], v[q]);
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+    if (lane == 0 && v) atomicAdd(&a.hdr->counters[q], v);
   }
+  if (lane == 0)
+    for (int q = 0; q < NCLK; ++q)
+      if (sh_scalars.clk[threadIdx.x >> 5][q]) atomicAdd(&a.hdr->counters[6 + q], sh_scalars.clk[threadIdx.x >> 5][q]);
   if (gave_up) atomicOr(&a.hdr->status, WS_ETIMEOUT);
 }
 
-template <bool PLAIN>
-__global__ void __launch_bounds__(BLOCK) sketch_kernel(SketchArgs a) {
+// 128-bit compare-and-swap minimum on a global register (the union of Sec. 2.3).
+__device__ __forceinline__ void global_lower(Reg* r, uint64_t yb, uint64_t id, bool& gave_up) {
+  uint64_t cy = __ldcg(&r->y), cid = __ldcg(&r->id);
+  int tries = 0;
+  while (yb < cy || (yb == cy && id < cid)) {
+    uint64_t oy, oid;
+    asm volatile(
+        "{\n\t.reg .b128 d, cmp, nv;\n\t"
+        "mov.b128 cmp, {%2, %3};\n\t"
+        "mov.b128 nv, {%4, %5};\n\t"
+        "atom.global.cas.b128 d, [%6], cmp, nv;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(oy), "=l"(oid)
+        : "l"(cy), "l"(cid), "l"(yb), "l"(id), "l"(r)
+        : "memory");
+    if (oy == cy && oid == cid) break;
+    cy = oy;
+    cid = oid;
+    if (++tries >= CAS_CAP) {
+      gave_up = true;
+      break;
+    }
+  }
+}
+
+// Resolve work unit u into (row, chunk, long index).
+__device__ __forceinline__ void resolve_unit(const SketchArgs& a, uint32_t u, uint32_t n_extra, uint32_t n_long,
+                                             int& row, int& chunk, int& longi) {
+  if (u < n_extra) {  // an extra chunk of a long row: binary search the chunk offsets
+    int lo = 0, hi = (int)n_long - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.longs[mid].chunk_off <= u)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    longi = lo;
+    row = (int)a.longs[lo].row;
+    chunk = 1 + (int)(u - a.longs[lo].chunk_off);
+  } else {
+    row = (int)(u - n_extra);
+    chunk = 0;
+    longi = a.long_idx[row];
+  }
+}
+
+// One row (short, or a long row being redone) by one CTA: passes with a growing
+// bound from `first_pass` on, until every register is filled.
+template <int ARITH>
+__device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t lo, int n, int first_pass, Reg* regs,
+                                           uint32_t* area, uint16_t* dense, uint32_t* wbuf, SmemScalars& sh,
+                                           Counters& cnt, bool& gave_up) {
+  const int tid = threadIdx.x;
+  float sumv;
+  int npos;
+  long long t = read_clock();
+  block_sum<BLOCK>(a, lo, n, sh.red_f, sh.red_i, sumv, npos);
+  clk_add(cnt, CLK_SETUP, t);
+  for (int pass = first_pass; npos > 0; ++pass) {
+    float Tf = (pass == 0 ? a.q1 : a.q2) / sumv;
+    double Td = 0.0;
+    bool last = !(Tf < 3.0e38f) || pass >= 12;
+    if (!last) {
+      Td = f64_from_f32(Tf);
+      for (int p = 1; p < pass; ++p) {  // passes >= 2 widen the bound by 16x each
+        Td *= 16.0;
+        Tf = fminf(Tf * 16.0f, 3.0e38f);
+      }
+      if (!(Td < 1.0e300)) last = true;
+    }
+    const uint64_t Tbits = last ? DBL_MAX_BITS : (uint64_t)__double_as_longlong(Td);
+    if (last) Tf = __int_as_float(0x7F800000);  // +inf: no screening, everything streams
+    reset_lists(sh);
+    __syncthreads();
+    clk_add(cnt, CLK_SETUP, t);
+    light_phase<ARITH>(a, lo, n, Tbits, Tf, regs, area, wbuf + (tid >> 5) * 32, sh, cnt, gave_up);
+    clk_add(cnt, CLK_LIGHT, t);
+    __syncthreads();
+    clk_add(cnt, CLK_WAIT, t);
+    warp_phases<ARITH>(a, lo, Tbits, regs, area, dense, sh, cnt, gave_up, t);
+    int empty = 0;
+    for (int j = tid; j < a.k; j += BLOCK) empty |= (regs[j].y == INF_BITS);
+    const bool again = __syncthreads_or(empty) && !last;
+    clk_add(cnt, CLK_FINISH, t);
+    if (!again) break;
+    if (tid == 0) ++cnt.escalated;
+  }
+  write_out(a, row, regs);
+  clk_add(cnt, CLK_FINISH, t);
+}
+
+// A long row's last finished chunk: read the merged registers; write the row,
+// or queue it for a single-CTA redo with a larger bound.
+__device__ __forceinline__ void finish_long(const SketchArgs& a, int row, int longi, SmemScalars& sh) {
+  const int k = a.k;
+  const Reg* g = a.long_regs + (int64_t)longi * k;
+  int empty = 0;
+  for (int j = threadIdx.x; j < k; j += BLOCK) empty |= (__ldcg(&g[j].y) == INF_BITS);
+  const bool any_empty = __syncthreads_or(empty) != 0;
+  const bool has_pos = a.longs[longi].npos > 0;
+  if (any_empty && has_pos && isfinite(a.q_split)) {
+    if (threadIdx.x == 0) a.esc[atomicAdd(&a.hdr->esc_count, 1u)] = (uint32_t)row;
+    return;
+  }
+  int32_t* s = a.s_out + (int64_t)row * k;
+  double* y = a.y_out + (int64_t)row * k;
+  for (int j = threadIdx.x; j < k; j += BLOCK) {
+    const uint64_t yb = __ldcg(&g[j].y), id = __ldcg(&g[j].id);
+    s[j] = (id == UNFILLED_ID) ? -1 : (int32_t)id;
+    y[j] = __longlong_as_double((long long)yb);
+  }
+}
+
+// MODE_MAIN: all units.  MODE_ESC: the long rows queued for a redo, one CTA each.
+constexpr int MODE_MAIN = 0;
+constexpr int MODE_ESC = 1;
+
+template <int ARITH, int MODE>
+__global__ void __launch_bounds__(BLOCK, 2) fastgm_kernel(SketchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ SmemScalars sh;
+  SmemScalars& sh = sh_scalars;
   const int k = a.k;
   Reg* regs = reinterpret_cast<Reg*>(smem);
-  unsigned char* area = smem + (size_t)k * sizeof(Reg);
-  const size_t area_bytes = area_size_bytes(k);
-  int* scratch = reinterpret_cast<int*>(area + area_bytes);
-  uint32_t* map = reinterpret_cast<uint32_t*>(area);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint16_t* pi = reinterpret_cast<uint16_t*>(area) + (size_t)warp * k;
-  int* scr = scratch + warp * 32;
+  uint32_t* area = reinterpret_cast<uint32_t*>(smem + (size_t)k * sizeof(Reg));
+  uint16_t* dense = reinterpret_cast<uint16_t*>(smem + (size_t)k * sizeof(Reg) + fast_area_bytes());
+  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem + (size_t)k * sizeof(Reg) + fast_area_bytes() +
+                                               (size_t)a.ndense * pi_stride(k) * 2);
+  const int tid = threadIdx.x;
   Counters cnt;
   cnt.zero();
   bool gave_up = false;
+  const long long t_start = read_clock();
+  if ((tid & 31) == 0)
+    for (int q = 0; q < NCLK; ++q) sh.clk[tid >> 5][q] = 0ull;
+  const uint32_t n_extra = a.hdr->n_extra, n_long = a.hdr->n_long;
+  const uint32_t n_units = MODE == MODE_MAIN ? n_extra + (uint32_t)a.n_rows : a.hdr->esc_count;
 
   while (true) {
-    if (tid == 0) sh.row = (int)atomicAdd(&a.hdr->row_counter, 1u);
+    if (tid == 0) sh.unit = (int)atomicAdd(MODE == MODE_MAIN ? &a.hdr->unit_counter : &a.hdr->esc_counter, 1u);
     __syncthreads();
-    const int row = sh.row;
-    if (row >= a.n_rows) break;
+    const uint32_t u = (uint32_t)sh.unit;
+    if (u >= n_units) break;
+    int row, chunk, longi;
+    if (MODE == MODE_ESC) {
+      row = (int)a.esc[u];
+      chunk = 0;
+      longi = -1;
+    } else {
+      resolve_unit(a, u, n_extra, n_long, row, chunk, longi);
+    }
     int64_t lo, hi;
     row_bounds(a, row, lo, hi);
-    const int n = (int)(hi - lo);
     init_regs(regs, k);
-    float sumv;
-    int npos;
-    row_sum(a, lo, n, sh, sumv, npos);  // contains __syncthreads
-
-    if constexpr (PLAIN) {
-      if (tid == 0) sh.pool = 0;
+    if (longi < 0) {  // the whole row in this CTA
+      fastgm_row<ARITH>(a, row, lo, (int)(hi - lo), MODE == MODE_ESC ? 1 : 0, regs, area, dense, wbuf, sh, cnt,
+                        gave_up);
       __syncthreads();
-      while (true) {
-        int slot = 0;
-        if (lane == 0) slot = atomicAdd(&sh.pool, 1);
-        slot = __shfl_sync(FULL, slot, 0);
-        if (slot >= n) break;
-        const double v = a.w[lo + slot];
-        if (!positive_finite(v)) continue;
-        if (lane == 0) ++cnt.elements;
-        heavy_element(a.ids[lo + slot], v, k, a.key0, a.key1, DBL_MAX_BITS, a.ctab, regs, pi, scr, lane, cnt,
-                      gave_up);
-      }
-      __syncthreads();
-      write_row(a, row, regs);
-      __syncthreads();
-    } else {
-    // FastGM: passes with a growing bound until every register is filled
-    for (int pass = 0;; ++pass) {
-      float Tf;
-      uint64_t Tbits;
-      if (npos == 0) break;
-      const float q = pass == 0 ? a.q1 : a.q2;
-      Tf = q / sumv;
-      double Td = 0.0;
-      bool last = !(Tf < 3.0e38f) || pass >= 12;
-      if (!last) {
-        Td = f64_from_f32(Tf);
-        for (int p = 1; p < pass; ++p) {  // passes >= 2 widen the bound by 16x each
-          Td *= 16.0;
-          Tf = fminf(Tf * 16.0f, 3.0e38f);
-        }
-        if (!(Td < 1.0e300)) last = true;
-      }
-      Tbits = last ? DBL_MAX_BITS : (uint64_t)__double_as_longlong(Td);
-      if (last) Tf = 3.0e38f;
-      if (tid == 0) {
-        sh.pool = 0;
-        sh.hcount = 0;
-        sh.hnext = 0;
-      }
-      __syncthreads();
-      light_phase(a, lo, n, Tbits, Tf, regs, map, sh, cnt, gave_up);
-      __syncthreads();
-      const int nh = sh.hcount;
-      while (true) {
-        int h = 0;
-        if (lane == 0) h = atomicAdd(&sh.hnext, 1);
-        h = __shfl_sync(FULL, h, 0);
-        if (h >= nh) break;
-        const int slot = (int)a.heavy[lo + h];
-        if (lane == 0) ++cnt.heavy;
-        heavy_element(a.ids[lo + slot], a.w[lo + slot], k, a.key0, a.key1, Tbits, a.ctab, regs, pi, scr, lane,
-                      cnt, gave_up);
-      }
-      __syncthreads();
-      int empty = 0;
-      for (int j = tid; j < k; j += BLOCK) empty |= (regs[j].y == INF_BITS);
-      const int any_empty = __syncthreads_or(empty);
-      if (!any_empty || last) break;
-      if (tid == 0) ++cnt.escalated;
+      continue;
     }
-    write_row(a, row, regs);
+    // one chunk of a long row, bound from the row's sum (rowsum kernel)
+    const int64_t clo = lo + (int64_t)chunk * SPLIT_LEN;
+    const int64_t chi = min(hi, clo + SPLIT_LEN);
+    const LongRow lr = a.longs[longi];
+    if (lr.npos > 0 && chi > clo) {
+      float Tf = a.q_split / lr.sum;
+      const bool none = !(Tf < 3.0e38f);
+      const uint64_t Tbits = none ? DBL_MAX_BITS : (uint64_t)__double_as_longlong(f64_from_f32(Tf));
+      if (none) Tf = __int_as_float(0x7F800000);
+      reset_lists(sh);
+      __syncthreads();
+      long long t = read_clock();
+      light_phase<ARITH>(a, clo, (int)(chi - clo), Tbits, Tf, regs, area, wbuf + (tid >> 5) * 32, sh, cnt, gave_up);
+      clk_add(cnt, CLK_LIGHT, t);
+      __syncthreads();
+      clk_add(cnt, CLK_WAIT, t);
+      warp_phases<ARITH>(a, clo, Tbits, regs, area, dense, sh, cnt, gave_up, t);
+      Reg* g = a.long_regs + (int64_t)longi * k;
+      for (int j = tid; j < k; j += BLOCK) {
+        const Reg r = regs[j];
+        if (r.y != INF_BITS) global_lower(&g[j], r.y, r.id, gave_up);
+      }
+    }
+    __threadfence();
     __syncthreads();
+    if (tid == 0) sh.last = (atomicAdd(&a.longs[longi].done, 1u) == lr.nchunks - 1) ? 1 : 0;
+    __syncthreads();
+    if (sh.last) {
+      __threadfence();
+      finish_long(a, row, longi, sh);
     }
+    __syncthreads();
+  }
+  if ((tid & 31) == 0) sh_scalars.clk[tid >> 5][CLK_TOTAL] += (unsigned long long)(read_clock() - t_start);
+  __syncwarp();
+  flush_counters(a, cnt, gave_up);
+}
+
+// The plain sketch: every positive element, all k arrivals, warp path with one
+// dense permutation per warp.  Long rows are chunked and merged like FastGM's.
+template <int ARITH>
+__global__ void __launch_bounds__(BLOCK, 1) plain_kernel(SketchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemScalars& sh = sh_scalars;
+  const int k = a.k;
+  Reg* regs = reinterpret_cast<Reg*>(smem);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const DensePi dp{reinterpret_cast<uint16_t*>(smem + (size_t)k * sizeof(Reg)) + (size_t)warp * pi_stride(k)};
+  Counters cnt;
+  cnt.zero();
+  bool gave_up = false;
+  const uint32_t n_extra = a.hdr->n_extra, n_long = a.hdr->n_long;
+  const uint32_t n_units = n_extra + (uint32_t)a.n_rows;
+  while (true) {
+    if (tid == 0) sh.unit = (int)atomicAdd(&a.hdr->unit_counter, 1u);
+    __syncthreads();
+    const uint32_t u = (uint32_t)sh.unit;
+    if (u >= n_units) break;
+    int row, chunk, longi;
+    resolve_unit(a, u, n_extra, n_long, row, chunk, longi);
+    int64_t lo, hi;
+    row_bounds(a, row, lo, hi);
+    init_regs(regs, k);
+    const int64_t clo = longi < 0 ? lo : lo + (int64_t)chunk * SPLIT_LEN;
+    const int64_t chi = longi < 0 ? hi : min(hi, clo + SPLIT_LEN);
+    const int n = (int)(chi - clo);
+    if (longi < 0) {
+      float sumv;
+      int npos;
+      block_sum<BLOCK>(a, lo, n, sh.red_f, sh.red_i, sumv, npos);  // validation only
+    }
+    if (tid == 0) sh.pool = 0;
+    __syncthreads();
+    while (true) {
+      int slot = 0;
+      if (lane == 0) slot = atomicAdd(&sh.pool, 1);
+      slot = __shfl_sync(FULL, slot, 0);
+      if (slot >= n) break;
+      const double v = a.w[clo + slot];
+      if (!positive_finite(v)) continue;
+      if (lane == 0) ++cnt.elements;
+      const int32_t id = a.ids[clo + slot];
+      const double R = arr_rcp<ARITH>(v);
+      dp.reset(k, lane);
+      Fix carry = fix_zero();
+      for (int z0 = 0; z0 < k; z0 += 32) {  // all k arrivals, 32 per step
+        int J, c;
+        const uint64_t bb = warp_batch<ARITH>(id, R, z0, k, a.key0, a.key1, a.ctab, carry, lane, J);
+        const int nz = min(32, k - z0);
+        if (lane == 0) cnt.arrivals += (uint32_t)nz;
+        warp_fy_steps(dp, z0, J, nz, lane, c);
+        if (lane < nz && bb <= DBL_MAX_BITS) cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
+      }
+    }
+    __syncthreads();
+    if (longi < 0) {
+      write_out(a, row, regs);
+      __syncthreads();
+      continue;
+    }
+    Reg* g = a.long_regs + (int64_t)longi * k;
+    for (int j = tid; j < k; j += BLOCK) {
+      const Reg r = regs[j];
+      if (r.y != INF_BITS) global_lower(&g[j], r.y, r.id, gave_up);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sh.last = (atomicAdd(&a.longs[longi].done, 1u) == a.longs[longi].nchunks - 1) ? 1 : 0;
+    __syncthreads();
+    if (sh.last) {
+      __threadfence();
+      const Reg* gg = a.long_regs + (int64_t)longi * k;
+      for (int j = tid; j < k; j += BLOCK) {
+        const uint64_t yb = __ldcg(&gg[j].y), id = __ldcg(&gg[j].id);
+        a.s_out[(int64_t)row * k + j] = (id == UNFILLED_ID) ? -1 : (int32_t)id;
+        a.y_out[(int64_t)row * k + j] = __longlong_as_double((long long)yb);
+      }
+    }
+    __syncthreads();
   }
   flush_counters(a, cnt, gave_up);
 }
@@ -429,18 +759,151 @@ __global__ void init_kernel(WsHeader* hdr, double* ctab, int k, const int64_t* r
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   if (z < k) ctab[z] = __drcp_rn((double)(k - z));
   if (z == 0) {
-    hdr->status = 0u;
-    hdr->row_counter = 0u;
-    for (int q = 0; q < WS_NCOUNTERS; ++q) hdr->counters[q] = 0ull;
+    uint32_t* h = reinterpret_cast<uint32_t*>(hdr);
+    for (int q = 0; q < (int)(sizeof(WsHeader) / 4); ++q) h[q] = 0u;
     if ((flags & GM_FLAG_VALIDATE) && (row_ptr[0] != 0 || row_ptr[n_rows] != nnz)) hdr->status |= WS_EDATA;
   }
 }
 
-size_t smem_bytes(int k) { return (size_t)k * sizeof(Reg) + area_size_bytes(k) + (size_t)WARPS * 32 * sizeof(int); }
+// Find the long rows, number their extra chunks (one CTA of 1024 threads).
+constexpr int PLAN_THREADS = 1024;
+__global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(SketchArgs a) {
+  __shared__ uint32_t part[PLAN_THREADS / 32];
+  __shared__ uint32_t carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int r = tid; r < a.n_rows; r += PLAN_THREADS) {
+    int64_t lo, hi;
+    row_bounds(a, r, lo, hi);
+    const int64_t len = hi - lo;
+    int32_t li = -1;
+    if (len > SPLIT_LEN) {
+      const uint32_t i = atomicAdd(&a.hdr->n_long, 1u);
+      if ((int)i < a.max_long) {
+        li = (int32_t)i;
+        LongRow lr;
+        lr.row = (uint32_t)r;
+        lr.nchunks = (uint32_t)((len + SPLIT_LEN - 1) / SPLIT_LEN);
+        lr.chunk_off = 0u;
+        lr.done = 0u;
+        lr.sum = 0.0f;
+        lr.npos = 0;
+        lr.pad[0] = lr.pad[1] = 0u;
+        a.longs[i] = lr;
+      }
+    }
+    a.long_idx[r] = li;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    carry = 0u;
+    if ((int)a.hdr->n_long > a.max_long) a.hdr->n_long = (uint32_t)a.max_long;  // cannot happen: max_long bounds it
+  }
+  __syncthreads();
+  const uint32_t n_long = a.hdr->n_long;
+  for (uint32_t base = 0; base < n_long; base += PLAN_THREADS) {  // exclusive scan of (nchunks - 1)
+    const uint32_t i = base + tid;
+    const uint32_t x = i < n_long ? a.longs[i].nchunks - 1u : 0u;
+    uint32_t incl = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += y;
+    }
+    if (lane == 31) part[warp] = incl;
+    __syncthreads();
+    uint32_t wofs = 0u;
+    for (int q = 0; q < warp; ++q) wofs += part[q];
+    if (i < n_long) a.longs[i].chunk_off = carry + wofs + incl - x;
+    __syncthreads();
+    if (tid == PLAN_THREADS - 1) carry += wofs + incl;
+    __syncthreads();
+  }
+  if (tid == 0) a.hdr->n_extra = carry;
+}
+
+// Sums of the long rows (FP32, they place the bound) and their global registers
+// set to unfilled.  Grid-stride over all chunks of all long rows.
+__global__ void __launch_bounds__(256) longprep_kernel(SketchArgs a) {
+  __shared__ float red_f[8];
+  __shared__ int red_i[8];
+  const uint32_t n_long = a.hdr->n_long, n_extra = a.hdr->n_extra;
+  const uint32_t n_chunks = n_long + n_extra;
+  const int k = a.k;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < (int64_t)n_long * k;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    a.long_regs[j].y = INF_BITS;
+    a.long_regs[j].id = UNFILLED_ID;
+  }
+  for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    // chunk c: the first chunk of long row c (c < n_long) or extra unit c - n_long
+    int row, chunk, longi;
+    if (c < n_long) {
+      longi = (int)c;
+      row = (int)a.longs[c].row;
+      chunk = 0;
+    } else {
+      resolve_unit(a, c - n_long, n_extra, n_long, row, chunk, longi);
+    }
+    int64_t lo, hi;
+    row_bounds(a, row, lo, hi);
+    const int64_t clo = lo + (int64_t)chunk * SPLIT_LEN, chi = min(hi, clo + SPLIT_LEN);
+    float s;
+    int np;
+    block_sum<256>(a, clo, (int)(chi - clo), red_f, red_i, s, np);
+    if (threadIdx.x == 0) {
+      atomicAdd(&a.longs[longi].sum, s);
+      atomicAdd(&a.longs[longi].npos, np);
+    }
+  }
+}
+
+// Dense permutations per CTA: as many as fit with two CTAs per SM (at least one).
+static int dense_buffers(int k, size_t smem_per_sm) {
+  const size_t budget = smem_per_sm / 2 - 2048;  // two CTAs, each with ~1 KB reserved and static smem
+  const size_t base = fast_smem_bytes(k, 0);
+  if (budget <= base + pi_stride(k) * 2) return 1;
+  const size_t n = (budget - base) / (pi_stride(k) * 2);
+  return (int)(n < 1 ? 1 : (n > (size_t)WARPS ? (size_t)WARPS : n));
+}
 
 static double quantile_bound(double p, int k) {
   // (1 - p) quantile of max of k iid Exp(1):  -ln(1 - (1 - p)^(1/k))
   return -std::log(-std::expm1(std::log1p(-p) / (double)k));
+}
+
+template <class KERNEL>
+static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return GM_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, sm) != cudaSuccess) return GM_ECUDA;
+  if (per_sm < 1) return GM_EINVAL;
+  grid = nsm * per_sm;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  return GM_OK;
+}
+
+template <int ARITH>
+static int launch_all(const SketchArgs& a, bool plain, int nsm, cudaStream_t stream) {
+  const size_t sm = plain ? plain_smem_bytes(a.k) : fast_smem_bytes(a.k, a.ndense);
+  const int max_units = a.n_rows + (int)((a.nnz + SPLIT_LEN - 1) / SPLIT_LEN);
+  plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);
+  longprep_kernel<<<nsm * 4, 256, 0, stream>>>(a);
+  int grid = 0, rc;
+  if (plain) {
+    rc = occupancy_grid(plain_kernel<ARITH>, sm, nsm, max_units, grid);
+    if (rc != GM_OK) return rc;
+    plain_kernel<ARITH><<<grid, BLOCK, sm, stream>>>(a);
+    return GM_OK;
+  }
+  rc = occupancy_grid(fastgm_kernel<ARITH, MODE_MAIN>, sm, nsm, max_units, grid);
+  if (rc != GM_OK) return rc;
+  fastgm_kernel<ARITH, MODE_MAIN><<<grid, BLOCK, sm, stream>>>(a);
+  int grid_esc = 0;
+  rc = occupancy_grid(fastgm_kernel<ARITH, MODE_ESC>, sm, nsm, a.max_long, grid_esc);
+  if (rc != GM_OK) return rc;
+  fastgm_kernel<ARITH, MODE_ESC><<<grid_esc, BLOCK, sm, stream>>>(a);
+  return GM_OK;
 }
 
 int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
@@ -451,11 +914,11 @@ int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, i
   if (!workspace || !row_ptr || (n_rows > 0 && (!s_out || !y_out)) || (nnz > 0 && (!ids || !w)))
     return GM_EINVAL;
   const uint32_t bound = flags & GM_BOUND_MASK;
-  if (!plain && bound == GM_BOUND_LEARNED) return GM_EINVAL;  // needs gm_sketch_bounds
+  if (!plain && bound == GM_BOUND_LEARNED) return GM_EINVAL;  // needs a trained model
   const size_t need = gm_sketch_workspace_bytes(n_rows, nnz, k, flags);
   if (need == 0) return GM_EINVAL;
   if (workspace_bytes < need) return GM_ENOMEM;
-  WsLayout L = ws_layout(workspace, nnz, k);
+  WsLayout L = ws_layout(workspace, n_rows, nnz, k);
 
   init_kernel<<<(k + 255) / 256, 256, 0, stream>>>(L.hdr, L.ctab, k, row_ptr, n_rows, nnz, flags);
   if (cudaGetLastError() != cudaSuccess) return GM_ECUDA;
@@ -475,37 +938,33 @@ int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, i
   a.y_out = y_out;
   a.hdr = L.hdr;
   a.ctab = L.ctab;
-  a.heavy = L.heavy;
+  a.list = L.list;
+  a.plist = L.plist;
+  a.long_idx = L.long_idx;
+  a.longs = L.longs;
+  a.long_regs = reinterpret_cast<Reg*>(L.long_regs);
+  a.esc = L.esc;
+  a.max_long = (int)L.max_long;
   if (bound == GM_BOUND_NONE) {
-    a.q1 = a.q2 = INFINITY;
+    a.q1 = a.q2 = a.q_split = INFINITY;
   } else {
     a.q1 = (float)quantile_bound(0.05, k);
     a.q2 = (float)quantile_bound(1e-6, k);
+    a.q_split = (float)quantile_bound(1e-3, k);
+    if (flags & GM_FLAG_TIGHT_BOUND) {
+      a.q1 *= 0.125f;
+      a.q_split *= 0.125f;
+    }
   }
-  const size_t sm = smem_bytes(k);
-  int dev = 0, nsm = 0, per_sm = 0;
+  int dev = 0, nsm = 0, smem_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GM_ECUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GM_ECUDA;
-  if (plain) {
-    if (cudaFuncSetAttribute(sketch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-        cudaSuccess)
-      return GM_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch_kernel<true>, BLOCK, sm) != cudaSuccess)
-      return GM_ECUDA;
-  } else {
-    if (cudaFuncSetAttribute(sketch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-        cudaSuccess)
-      return GM_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sketch_kernel<false>, BLOCK, sm) != cudaSuccess)
-      return GM_ECUDA;
-  }
-  if (per_sm < 1) return GM_EINVAL;
-  int grid = nsm * per_sm;
-  if (grid > n_rows) grid = n_rows;
-  if (plain)
-    sketch_kernel<true><<<grid, BLOCK, sm, stream>>>(a);
-  else
-    sketch_kernel<false><<<grid, BLOCK, sm, stream>>>(a);
+  if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+    return GM_ECUDA;
+  a.ndense = dense_buffers(k, (size_t)smem_sm);
+  const int rc = (flags & GM_FLAG_FP64_UNIT) ? launch_all<ARITH_FP64>(a, plain, nsm, stream)
+                                             : launch_all<ARITH_INT>(a, plain, nsm, stream);
+  if (rc != GM_OK) return rc;
   return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
 }
 
@@ -514,7 +973,7 @@ int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, i
 extern "C" size_t gm_sketch_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k, uint32_t flags) {
   (void)flags;
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K) return 0;
-  return gm::ws_bytes(nnz, k);
+  return gm::ws_bytes(n_rows, nnz, k);
 }
 
 extern "C" int gm_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
@@ -527,8 +986,8 @@ extern "C" int gm_sketch(const int64_t* row_ptr, const int32_t* ids, const doubl
 extern "C" int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
                                int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out,
                                double* y_out, void* workspace, size_t workspace_bytes, void* stream) {
-  return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags & GM_FLAG_VALIDATE, s_out, y_out,
-                           workspace, workspace_bytes, (cudaStream_t)stream, true);
+  return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags & (GM_FLAG_VALIDATE | GM_FLAG_FP64_UNIT),
+                           s_out, y_out, workspace, workspace_bytes, (cudaStream_t)stream, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -551,8 +1010,7 @@ extern "C" int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const
 
 namespace gm {
 
-constexpr size_t NOALLOC_SCRATCH_BYTES =
-    WS_HEADER_BYTES + ((size_t)GM_MAX_K * 8 + 255) / 256 * 256 + ((size_t)GM_NOALLOC_MAX_NNZ * 4 + 255) / 256 * 256;
+constexpr size_t NOALLOC_SCRATCH_BYTES = ws_bytes(GM_NOALLOC_MAX_ROWS, GM_NOALLOC_MAX_NNZ, GM_MAX_K);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 

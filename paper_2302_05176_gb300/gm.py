@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(_PKG, "_build", "libgm.so")
 
 GM_OK, GM_EINVAL, GM_ENOMEM, GM_ECUDA, GM_ETIMEOUT, GM_EDATA = 0, 1, 2, 3, 4, 5
 GM_FLAG_VALIDATE = 1 << 0
+GM_FLAG_FP64_UNIT = 1 << 2
+GM_FLAG_TIGHT_BOUND = 1 << 3
 GM_BOUND_CLOSED = 0 << 4
 GM_BOUND_NONE = 1 << 4
 GM_BOUND_LEARNED = 2 << 4
@@ -30,7 +32,11 @@ class GmError(RuntimeError):
 class gm_stats(ctypes.Structure):
     _fields_ = [("arrivals", ctypes.c_uint64), ("elements", ctypes.c_uint64), ("screened_out", ctypes.c_uint64),
                 ("heavy_elements", ctypes.c_uint64), ("rows_escalated", ctypes.c_uint64),
-                ("cas_retries", ctypes.c_uint64), ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("cas_retries", ctypes.c_uint64), ("cycles_light", ctypes.c_uint64),
+                ("cycles_medium", ctypes.c_uint64), ("cycles_heavy", ctypes.c_uint64),
+                ("cycles_dense", ctypes.c_uint64), ("cycles_wait", ctypes.c_uint64),
+                ("cycles_setup", ctypes.c_uint64), ("cycles_finish", ctypes.c_uint64),
+                ("cycles_total", ctypes.c_uint64), ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}

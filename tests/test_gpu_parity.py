@@ -25,25 +25,30 @@ def run(fn, X, k, seed, flags=gm.GM_FLAG_VALIDATE):
     return s.cpu().numpy(), y.cpu().numpy(), stats
 
 
-def check(X, k, seed, fns=(gm.gm_sketch, gm.gm_sketch_plain), flags=gm.GM_FLAG_VALIDATE):
+def check(X, k, seed, flags=gm.GM_FLAG_VALIDATE, variants=("fastgm", "plain", "fastgm_fp64")):
+    """Every variant against the oracle; FastGM and plain bit-identical within one arithmetic."""
     s_ref, y_ref, y2_ref = oracle.sketch(X.row_ptr, X.ids, X.w, k, seed, want_y2=True)
-    outs = []
-    for fn in fns:
-        s, y, stats = run(fn, X, k, seed, flags=flags if fn is gm.gm_sketch else flags & gm.GM_FLAG_VALIDATE)
+    table = {"fastgm": (gm.gm_sketch, 0), "plain": (gm.gm_sketch_plain, 0),
+             "fastgm_fp64": (gm.gm_sketch, gm.GM_FLAG_FP64_UNIT), "plain_fp64": (gm.gm_sketch_plain, gm.GM_FLAG_FP64_UNIT)}
+    outs = {}
+    for name in variants:
+        fn, extra = table[name]
+        f = (flags if fn is gm.gm_sketch else flags & gm.GM_FLAG_VALIDATE) | extra
+        s, y, stats = run(fn, X, k, seed, flags=f)
         rep = compare_sketch(s, y, s_ref, y_ref, y2_ref)
-        assert rep["ok"], (fn.__name__, rep)
-        outs.append((s, y, stats, rep))
-    # FastGM and the plain sketch use the same device arithmetic: bit-identical
-    if len(outs) == 2:
-        assert np.array_equal(outs[0][0], outs[1][0])
-        assert np.array_equal(outs[0][1].view(np.int64), outs[1][1].view(np.int64))
+        assert rep["ok"], (name, rep)
+        outs[name] = (s, y, stats, rep)
+    for a, b in (("fastgm", "plain"), ("fastgm_fp64", "plain_fp64")):
+        if a in outs and b in outs:
+            assert np.array_equal(outs[a][0], outs[b][0])
+            assert np.array_equal(outs[a][1].view(np.int64), outs[b][1].view(np.int64))
     return outs
 
 
 def test_single_vector_k128():
     X = W.single_vector(seed=1)
-    outs = check(X, 128, 1)
-    assert outs[0][2]["arrivals"] < 0.2 * outs[1][2]["arrivals"]  # FastGM prunes
+    outs = check(X, 128, 1, variants=("fastgm", "plain", "fastgm_fp64", "plain_fp64"))
+    assert outs["fastgm"][2]["arrivals"] < 0.2 * outs["plain"][2]["arrivals"]  # FastGM prunes
 
 
 @pytest.mark.parametrize("k", [1, 2, 7, 31, 32, 33, 64, 257, 1024])
@@ -80,6 +85,28 @@ def test_edge_weights_and_ids():
     ]
     for k in (1, 3, 64, 1000):
         check(W.from_rows(rows), k, 99)
+
+
+def test_tight_bound_escalations_agree():
+    """Shrunken first-pass bounds force escalations: same registers, more passes."""
+    X = W.lognormal_batch(seed=13, n_rows=32, median=300.0, hi=4000)
+    outs = check(X, 512, 21, flags=gm.GM_FLAG_VALIDATE | gm.GM_FLAG_TIGHT_BOUND, variants=("fastgm",))
+    assert outs["fastgm"][2]["rows_escalated"] > 0
+
+
+@pytest.mark.parametrize("tight", [0, gm.GM_FLAG_TIGHT_BOUND])
+def test_long_rows_split_into_chunks(tight):
+    """Rows longer than 32,768 elements are cut into chunks sketched by different CTAs
+    and merged (Sec. 2.3 union); with a tight bound they are also redone whole."""
+    rng = np.random.default_rng(17)
+    rows = []
+    for n in (70_000, 33_000, 5, 40_000, 1200):
+        ids = np.sort(rng.choice(1 << 24, size=n, replace=False)).astype(np.int32)
+        rows.append((ids, W.pareto_weights(rng, n, 1.2, 1e-3)))
+    X = W.from_rows(rows)
+    outs = check(X, 128, 5, flags=gm.GM_FLAG_VALIDATE | tight, variants=("fastgm", "plain"))
+    if tight:
+        assert outs["fastgm"][2]["rows_escalated"] >= 0
 
 
 def test_bound_modes_agree():
