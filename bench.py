@@ -35,7 +35,7 @@ HBM_FALLBACK_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=2)
@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--only", default="all", choices=["all", "fastgm"],
                     help="fastgm: time only the FastGM step (the case profiled with ncu)")
     ap.add_argument("--k", type=int, default=K_MAIN, help="k of the --only fastgm step")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-bound ablation")
+    ap.add_argument("--learned-rows", type=int, default=200_000, help="sketches in the bound network's training set")
+    ap.add_argument("--learned-steps", type=int, default=400, help="Adam steps of the bound network")
     ap.add_argument("--arith", action="store_true",
                     help="time the per-arrival arithmetic: FP64 unit vs integer pipes (diagnostic kernels)")
     return ap.parse_args()
@@ -115,6 +118,67 @@ class ClockSampler:
         reasons = [n for i, n in enumerate(names) if any(r[3 + i].lower().startswith("active") for r in rows)]
         return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": num(rows[0][1]), "reasons": reasons,
                 "samples": len(rows), "power_w_max": float(np.nanmax([num(r[2]) for r in rows]))}
+
+
+# Work units of the sketch kernel and their cost in lane-instructions, counted by
+# ncu (smsp__thread_inst_executed.sum) on gm_diag_arrival_cost's two kernels, which
+# run one arrival (Philox, -ln u, RN(E C_z), the exact sum, RN(S R), RandInt) and
+# one first-arrival screen per thread over 2^24 elements: 7,373,606,055 and
+# 1,477,443,584 lane-instructions.
+LANE_INST_PER_ARRIVAL = 7373606055 / 2 ** 24   # 439.5
+LANE_INST_PER_SCREEN = 1477443584 / 2 ** 24    # 88.1
+LANES_PER_SM = 128                              # 4 sub-partitions x 32 lanes issue per clock
+LAUNCHES_PER_CALL = 5                           # init, plan, long-row prep, main, long-row redo
+LEARNED_TAU = 0.95
+# DRAM bytes (read + write) of one main-kernel launch from ncu, valid only for the
+# kernel sources they were taken on (sha256 of csrc/, see kernel_source_sha).
+TRAFFIC = {"src_sha": None, "bytes": None}
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2302_05176_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def alu_roofline(st, kernel_ms):
+    """The main kernel against the integer/ALU issue roofline: algorithmic
+    lane-instructions (kept arrivals x 439.5 + screened elements x 88.1) per
+    second of the kernel alone, over 152 SMs x 128 lanes x the maximum SM clock."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    mhz = max_sm_clock_mhz()
+    peak = props.multi_processor_count * LANES_PER_SM * mhz * 1e6 / 1e12
+    work = st["kept"] * LANE_INST_PER_ARRIVAL + st["elements"] * LANE_INST_PER_SCREEN
+    achieved = work / (kernel_ms * 1e-3) / 1e12
+    traffic = TRAFFIC["bytes"] if TRAFFIC["src_sha"] == kernel_source_sha() else None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-inst/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "fastgm_kernel<1, 0>", "kernel_ms": kernel_ms,
+            "peak_source": "derived: %d SMs x %d lanes x %.0f MHz" % (props.multi_processor_count, LANES_PER_SM, mhz),
+            "work_lane_inst": work, "kept_arrivals": st["kept"], "screened_elements": st["elements"]}
+
+
+def max_sm_clock_mhz():
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(int(os.environ.get("LOCAL_RANK", 0))),
+                              "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        return float(out.splitlines()[0])
+    except Exception:
+        return 2070.0
+
+
+def hbm_figures(nnz, n_rows, k, kernel_ms):
+    hbm_gbs, src = peaks()
+    abytes = algorithmic_bytes(nnz, n_rows, k)
+    a = abytes / (kernel_ms * 1e-3) / 1e9
+    return {"achieved": a, "peak": hbm_gbs, "unit": "GB/s", "frac": a / hbm_gbs, "peak_source": src,
+            "algorithmic_bytes_per_launch": abytes}
 
 
 def algorithmic_bytes(nnz, n_rows, k):
@@ -190,6 +254,16 @@ def run_arith(args):
         out["neg_log_" + tag] = n / (time_ms(lambda: L.gm_diag_neglog(P(x), n, fp64, P(y), st)) * 1e-3)
         out["mul_" + tag] = n / (time_ms(lambda: L.gm_diag_dmul(P(a), P(b), n, fp64, P(y), st)) * 1e-3)
         out["rcp_" + tag] = n / (time_ms(lambda: L.gm_diag_drcp(P(a), n, fp64, P(y), st)) * 1e-3)
+    # one arrival / one screen in isolation (their instruction counts set the ALU roofline's work units)
+    L.gm_diag_arrival_cost.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, vp, vp, vp, vp,
+                                       ctypes.c_float, vp]
+    ids = torch.from_numpy(rng.integers(0, 2**31 - 1, size=n, dtype=np.int64).astype(np.int32)).cuda()
+    ctab = torch.empty(K_MAIN, dtype=torch.float64, device="cuda")
+    jout = torch.empty(n, dtype=torch.int32, device="cuda")
+    scr = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ms = time_ms(lambda: L.gm_diag_arrival_cost(P(ids), P(a), n, K_MAIN, SEED, P(ctab), P(y), P(jout), P(scr),
+                                                 1e-3, st))
+    out["arrival_and_screen_pairs"] = n / (ms * 1e-3)
     print(json.dumps(out), flush=True)
 
 
@@ -231,9 +305,11 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    import ctypes
     from paper_2302_05176_gb300 import gm
     from paper_2302_05176_gb300 import workloads as W
-    gm.lib()
+    L = gm.lib()
+    L.gm_diag_time_main_kernel.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
 
     # weak scaling: every rank sketches its own batch of the same shape
     X = W.lognormal_batch(seed=SEED + rank, n_rows=N_ROWS)
@@ -246,42 +322,62 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(fn, k, steps, warmup, flags=0):
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(call, k, steps, warmup, learned_ws=False):
+        """Time `steps` calls (after `warmup`) with CUDA events on the launching stream;
+        also the main sketch kernel alone, from events the library records around it."""
         s_out = torch.empty((n_rows, k), dtype=torch.int32, device="cuda")
         y_out = torch.empty((n_rows, k), dtype=torch.float64, device="cuda")
-        ws = gm.workspace(n_rows, nnz, k)
+        nbytes = gm.sketch_learned_workspace_bytes(n_rows, nnz, k) if learned_ws else \
+            gm.sketch_workspace_bytes(n_rows, nnz, k)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         for _ in range(warmup):
-            fn(rp, ids, w, k, SEED, flags=flags, s_out=s_out, y_out=y_out, ws=ws)
+            call(s_out, y_out, ws)
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in kev:  # materialise the event handles
+            a.record(stream)
+            b.record(stream)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(steps):
-            fn(rp, ids, w, k, SEED, flags=flags, s_out=s_out, y_out=y_out, ws=ws)
+        for a, b in kev:
+            L.gm_diag_time_main_kernel(a.cuda_event, b.cuda_event)
+            call(s_out, y_out, ws)
+        L.gm_diag_time_main_kernel(None, None)
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+        kms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in kev])))
         code, st = gm.gm_status(ws)
         if code != gm.GM_OK:
             raise RuntimeError("device status %s" % gm.strerror(code))
-        return ms, st
+        return ms, kms, st, s_out, y_out
+
+    def sketch_call(fn, k, flags=0):
+        return lambda s_out, y_out, ws: fn(rp, ids, w, k, SEED, flags=flags, s_out=s_out, y_out=y_out, ws=ws)
 
     if args.only == "fastgm":
-        ms, st = timed(gm.gm_sketch, args.k, args.steps, args.warmup)
+        ms, kms, st, _, _ = timed(sketch_call(gm.gm_sketch, args.k), args.k, args.steps, args.warmup)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": world * n_rows / (ms * 1e-3), "unit": "sketches/s",
-                              "ms_per_step": ms, "only": "fastgm k=%d" % args.k, "stats": st}), flush=True)
+                              "ms_per_step": ms, "kernel_ms": kms, "only": "fastgm k=%d" % args.k, "stats": st}),
+                  flush=True)
         return
     clocks = ClockSampler(local)
     clocks.start()
-    ms_main, st_main = timed(gm.gm_sketch, K_MAIN, args.steps, args.warmup)
+    ms_main, kms_main, st_main, s_main, y_main = timed(sketch_call(gm.gm_sketch, K_MAIN), K_MAIN, args.steps,
+                                                       args.warmup)
     clk = clocks.stop()
-    ms_alt, st_alt = timed(gm.gm_sketch, K_ALT, max(2, args.steps // 3), args.warmup)
-    ms_plain, st_plain = timed(gm.gm_sketch_plain, K_MAIN, args.plain_steps, 1)
+    ms_alt, kms_alt, st_alt, _, _ = timed(sketch_call(gm.gm_sketch, K_ALT), K_ALT, max(2, args.steps // 3),
+                                          args.warmup)
+    ms_plain, _, st_plain, _, _ = timed(sketch_call(gm.gm_sketch_plain, K_MAIN), K_MAIN, args.plain_steps, 1)
 
     # end to end through the C-ABI with host buffers: H2D of the inputs and D2H of the
     # registers inside the timed region, every step
@@ -310,45 +406,80 @@ def main():
     for _ in range(args.steps):
         e2e_step()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
     h2d = X.row_ptr.nbytes + X.ids.nbytes + X.w.nbytes
     d2h = n_rows * K_MAIN * (4 + 8)
 
-    hbm_gbs, peak_src = peaks()
-    abytes = algorithmic_bytes(nnz, n_rows, K_MAIN)
-    achieved = abytes / (ms_main * 1e-3) / 1e9
     value = world * n_rows / (ms_main * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "sketches/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_main, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "rows_per_gpu": n_rows, "nnz_per_gpu": nnz, "k": K_MAIN,
-                   "l2": "inputs %.0f MB > 129 MB L2; no flush" % (h2d / 1e6), "parallelism": "rows sharded, dp%d" % world},
+                   "l2": "inputs %.0f MB > 129 MB L2; no flush" % (h2d / 1e6),
+                   "parallelism": "rows sharded, dp%d" % world},
         "elements_per_s": world * nnz / (ms_main * 1e-3),
         "arrivals_per_sketch": st_main["arrivals"] / n_rows,
+        "kept_arrivals_per_sketch": st_main["kept"] / n_rows,
         "k4096": {"sketches_per_s": world * n_rows / (ms_alt * 1e-3), "ms_per_step": ms_alt,
-                  "elements_per_s": world * nnz / (ms_alt * 1e-3)},
+                  "elements_per_s": world * nnz / (ms_alt * 1e-3),
+                  "roofline_frac": alu_roofline(st_alt, kms_alt)["frac"]},
         "plain_k1024": {"sketches_per_s": world * n_rows / (ms_plain * 1e-3), "ms_per_step": ms_plain,
-                        "arrivals_per_s": st_plain["arrivals"] / (args.plain_steps + 1) / (ms_plain * 1e-3)},
+                        "arrivals_per_s": st_plain["arrivals"] / (ms_plain * 1e-3)},
         "speedup_vs_plain_k1024": ms_plain / ms_main,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
-                     "frac": achieved / hbm_gbs, "traffic": None, "peak_source": peak_src,
-                     "kernel": "sketch_kernel<false>", "algorithmic_bytes_per_launch": abytes},
+        "roofline": alu_roofline(st_main, kms_main),
+        "hbm": hbm_figures(nnz, n_rows, K_MAIN, kms_main),
         "e2e": {"value": world * n_rows / e2e_s, "unit": "sketches/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": LAUNCHES_PER_CALL * args.steps,
         "clocks": clk,
     }
+    if not args.no_learned:
+        line["learned_k1024"] = learned_ablation(args, timed, sketch_call, (rp, ids, w), s_main, y_main, ms_main,
+                                                 st_main, n_rows)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(X, K_MAIN, SEED, n_rows=args.cpu_rows)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def learned_ablation(args, timed, sketch_call, dev_csr, s_main, y_main, ms_main, st_main, n_rows):
+    """Train the bound network on sketches of fresh synthetic rows (k in {256, 1024,
+    4096}), then time FastGM with its bound, with the closed-form bound (the main
+    step) and with no initial bound on the benchmark batch; check all three agree."""
+    import torch
+    from paper_2302_05176_gb300 import gm, learned
+    rp, ids, w = dev_csr
+    t0 = time.perf_counter()
+    ts = learned.make_training_set(args.learned_rows, ks=(256, 1024, 4096), seed=1000)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    params, hist = learned.train(ts, tau=LEARNED_TAU, steps=args.learned_steps)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    model = learned.BoundModel(params, margin=0.0, tau=LEARNED_TAU)
+
+    ms_l, kms_l, st_l, s_l, y_l = timed(
+        lambda s_out, y_out, ws: model.sketch(rp, ids, w, K_MAIN, SEED, s_out=s_out, y_out=y_out, ws=ws),
+        K_MAIN, args.steps, args.warmup, learned_ws=True)
+    ms_n, kms_n, st_n, s_n, y_n = timed(sketch_call(gm.gm_sketch, K_MAIN, gm.GM_BOUND_NONE), K_MAIN,
+                                        max(2, args.steps // 3), args.warmup)
+    same = lambda s, y: bool(torch.equal(s, s_main) and torch.equal(y.view(torch.int64), y_main.view(torch.int64)))
+    return {
+        "train_sketches": int(ts.target.numel()), "train_set_s": t1 - t0, "train_s": t2 - t1,
+        "train_steps": args.learned_steps, "tau": LEARNED_TAU, "final_pinball_loss": hist[-1][1],
+        "sketches_per_s": n_rows / (ms_l * 1e-3), "ms_per_step": ms_l,
+        "fallback_rate": st_l["rows_fallback"] / n_rows,
+        "closed_form_fallback_rate": st_main["rows_fallback"] / n_rows,
+        "kept_arrivals_per_sketch": st_l["kept"] / n_rows,
+        "closed_form_kept_arrivals_per_sketch": st_main["kept"] / n_rows,
+        "no_bound": {"sketches_per_s": n_rows / (ms_n * 1e-3), "ms_per_step": ms_n,
+                     "kept_arrivals_per_sketch": st_n["kept"] / n_rows},
+        "speedup_vs_no_bound": ms_n / ms_l, "speedup_vs_closed_form": ms_main / ms_l,
+        "identical_to_closed_form": same(s_l, y_l), "no_bound_identical": same(s_n, y_n),
+    }
 
 
 if __name__ == "__main__":

@@ -91,6 +91,8 @@ typedef struct gm_stats {
    * setup (sums, bounds), row finish (filled check, output), total */
   uint64_t cycles_light, cycles_medium, cycles_heavy, cycles_dense, cycles_wait, cycles_setup, cycles_finish,
       cycles_total;
+  uint64_t kept;            /* arrivals within the bound (each updates a register)      */
+  uint64_t rows_fallback;   /* rows whose first-pass bound was below y* (redone wider)  */
   uint32_t status;          /* GM_OK, GM_EDATA or GM_ETIMEOUT                           */
   uint32_t reserved;
 } gm_stats;
@@ -204,6 +206,70 @@ int gm_cardinality(const double* y, int32_t n_rows, int32_t k, double* out, void
  */
 int gm_merge(const int32_t* s_a, const double* y_a, const int32_t* s_b, const double* y_b, int64_t n_regs,
              int32_t* s_out, double* y_out, void* stream);
+
+/* ---- learned pruning bound ---------------------------------------------------
+ * Not in the paper: a small MLP predicts, per row, the bound below which FastGM
+ * generates arrivals (the role of FastSearch's release horizon, Sec. 2.2).  Any
+ * bound gives the same registers; an unfilled row is redone with the closed-form
+ * bound and then wider ones, so the result stays exact.
+ *
+ * Model: 8 -> 64 -> 64 -> 1, GELU (erf form), FP32.  Parameters, one contiguous
+ * device float array of GM_MODEL_PARAMS: W1[64][8], b1[64], W2[64][64], b2[64],
+ * w3[64], b3.  The output is ln(bound) = net(x) - x[1]: the network sees the
+ * scale-free quantity ln(y* sum v) (scaling v by c scales y* by 1/c exactly).
+ * Features per row (float[8]): ln n+, ln sum v, ln max v, ln of the weights'
+ * 10/50/90/99 % quantiles (from a log2 histogram, 1/4-octave bins), ln k.
+ */
+#define GM_MODEL_FEATURES 8
+#define GM_MODEL_HIDDEN 64
+#define GM_MODEL_PARAMS (GM_MODEL_HIDDEN * GM_MODEL_FEATURES + GM_MODEL_HIDDEN + \
+                         GM_MODEL_HIDDEN * GM_MODEL_HIDDEN + GM_MODEL_HIDDEN + GM_MODEL_HIDDEN + 1)
+
+/* Features of every row into feats[n_rows * 8] (device).  Rows without positive
+ * weights get ln n+ = ln sum v = ... = -inf replaced by 0.  GM_EINVAL on bad sizes. */
+int gm_features(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz, int32_t k,
+                float* feats, void* stream);
+
+/* Per row, ln max_j y_j of a finished sketch (the training target), into
+ * ln_ystar[n_rows]; +inf when a register is unfilled.  k >= 1. */
+int gm_row_ln_ystar(const double* y, int32_t n_rows, int32_t k, float* ln_ystar, void* stream);
+
+/* Initialise params (device, GM_MODEL_PARAMS floats): uniform(-1/sqrt(fan_in),
+ * 1/sqrt(fan_in)) from a Philox stream keyed by `seed`, biases 0. */
+int gm_model_init(float* params, uint64_t seed, void* stream);
+
+/* out[i] = predicted ln bound of sample i (feats: float[n * 8]). */
+int gm_model_forward(const float* params, const float* feats, int32_t n, float* out, void* stream);
+
+/* Mean pinball loss at level tau (0 < tau < 1), L = mean_i rho_tau(t_i - pred_i)
+ * with rho_tau(r) = tau r for r > 0 and (tau - 1) r otherwise, of the prediction
+ * against target[n] (ln y*); its gradient into grad[GM_MODEL_PARAMS] (overwritten)
+ * and L into loss[1] (device).  At r = 0 the subgradient of the r <= 0 branch is
+ * taken.  The loss is minimised by the tau-quantile of ln y* given the features,
+ * so the bound exceeds y* in a fraction tau of rows.  n >= 1.  The result is the
+ * same bits on every run (fixed partition, fixed summation order).  Workspace:
+ * gm_model_grad_workspace_bytes() bytes of device scratch. */
+size_t gm_model_grad_workspace_bytes(void);
+int gm_model_grad(const float* params, const float* feats, const float* target, int32_t n, float tau, float* grad,
+                  float* loss, void* workspace, size_t workspace_bytes, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) of params with grad; adam holds
+ * 2 * GM_MODEL_PARAMS floats of moments (zero them before step 1); step >= 1. */
+int gm_model_adam(float* params, float* adam, const float* grad, float lr, int32_t step, void* stream);
+
+/* Save / load params to / from a file (host path; blocks on `stream`).  The file
+ * holds a 16-byte header ("GMMLP001", feature and hidden sizes) and the floats. */
+int gm_model_save(const float* params, const char* path, void* stream);
+int gm_model_load(float* params, const char* path, void* stream);
+
+/* gm_sketch with the first-pass bound of each row predicted by the model
+ * (features and inference run on `stream` ahead of the sketch kernels):
+ * T_r = exp(prediction_r + margin).  Same registers as gm_sketch.  Workspace:
+ * gm_sketch_learned_workspace_bytes(). */
+size_t gm_sketch_learned_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k);
+int gm_sketch_learned(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
+                      int32_t k, uint64_t seed, uint32_t flags, const float* params, float margin, int32_t* s_out,
+                      double* y_out, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Human-readable text of a status code (static storage, never NULL). */
 const char* gm_strerror(int code);

@@ -47,11 +47,27 @@ int gm_diag_arrivals(int32_t id, double v, int32_t k, uint64_t seed, int32_t n_s
 int gm_diag_first_arrival(const int32_t* ids, const double* v, int64_t n, int32_t k, uint64_t seed, float T,
                           uint8_t* screened, double* b0, void* stream);
 
+/* The algorithmic work of one arrival and of one first-arrival screen, each
+ * computed independently per element (for instruction counting): out[i] = the
+ * arrival time of step z = i mod k of element ids[i] with R = R[i] (a
+ * single-term sum), jout[i] its RandInt target, screened[i] the screen decision
+ * for weight R[i] and bound T.  ctab_scratch: >= k doubles.  1 <= k <= GM_MAX_K. */
+int gm_diag_arrival_cost(const int32_t* ids, const double* R, int64_t n, int32_t k, uint64_t seed,
+                         double* ctab_scratch, double* out, int32_t* jout, uint8_t* screened, float T,
+                         void* stream);
+
 /* blocks x 256 threads, each running 8 independent FMA chains of `iters` steps
  * in FP64 (fp64 = 1) or FP32 (fp64 = 0); out: device array of blocks*256
  * doubles (or floats).  Timed by the caller, it gives the device's FMA rate:
  * 8 * iters * blocks * 256 FMAs per launch. */
 int gm_diag_fma(int32_t fp64, int32_t blocks, int32_t iters, void* out, void* stream);
+
+/* Register two CUDA events (cudaEvent_t, created by the caller) that every later
+ * gm_sketch / gm_sketch_plain / gm_sketch_learned call records on its stream
+ * immediately before and after its main sketch kernel, so that kernel can be
+ * timed alone; (NULL, NULL) stops it.  Process-wide setting, not thread-safe:
+ * for timing only.  GM_EINVAL if exactly one of the two is NULL. */
+int gm_diag_time_main_kernel(void* before, void* after);
 
 #ifdef __cplusplus
 }

@@ -29,6 +29,8 @@ extern "C" int gm_status(const void* workspace, gm_stats* stats, void* stream) {
     stats->cycles_setup = h.counters[11];
     stats->cycles_finish = h.counters[12];
     stats->cycles_total = h.counters[13];
+    stats->kept = h.counters[14];
+    stats->rows_fallback = h.counters[15] + h.esc_count;
     stats->status = (uint32_t)code;
   }
   return code;

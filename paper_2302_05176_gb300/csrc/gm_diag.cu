@@ -85,6 +85,31 @@ __global__ void diag_fma_kernel(T* out, int iters, T a, T b) {
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+// One arrival's value chain per thread, each independent: Philox, -ln u, the
+// product by C_z, the exact sum (a single term), its rounding, the product by R
+// and RandInt -- the algorithmic work of one arrival, for instruction counting.
+__global__ void diag_arrival_cost_kernel(const int32_t* __restrict__ ids, const double* __restrict__ R, int64_t n,
+                                         int k, uint32_t key0, uint32_t key1, const double* __restrict__ ctab,
+                                         double* __restrict__ out, int32_t* __restrict__ jout) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int z = (int)(i % k);
+    const Words wd = philox((uint32_t)ids[i], (uint32_t)z, key0, key1);
+    Fix acc = fix_zero();
+    fix_add(acc, fix_from(dmul_normal(neglog_u(wd.w0, wd.w1), __ldg(ctab + z))));
+    out[i] = dmul_pos(fix_round(acc), R[i]);
+    jout[i] = randint(wd.w2, wd.w3, z, k);
+  }
+}
+
+// The first-arrival screen alone: Philox and the FP32 test, per element.
+__global__ void diag_screen_cost_kernel(const int32_t* __restrict__ ids, const double* __restrict__ v, int64_t n, int k,
+                                        uint32_t key0, uint32_t key1, float T, uint8_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Words wd = philox((uint32_t)ids[i], 0u, key0, key1);
+    out[i] = screen_out(wd.w1, f32_trunc(v[i]), T, (float)k) ? 1 : 0;
+  }
+}
+
 static size_t round16(size_t x) { return (x + 15) / 16 * 16; }
 
 static int grid_for(int64_t n) {
@@ -174,5 +199,19 @@ extern "C" int gm_diag_fma(int32_t fp64, int32_t blocks, int32_t iters, void* ou
     gm::diag_fma_kernel<double><<<blocks, 256, 0, st>>>((double*)out, iters, 0.999, 1e-3);
   else
     gm::diag_fma_kernel<float><<<blocks, 256, 0, st>>>((float*)out, iters, 0.999f, 1e-3f);
+  return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
+}
+
+extern "C" int gm_diag_arrival_cost(const int32_t* ids, const double* R, int64_t n, int32_t k, uint64_t seed,
+                                    double* ctab_scratch, double* out, int32_t* jout, uint8_t* screened,
+                                    float T, void* stream) {
+  if (n < 0 || k < 1 || k > GM_MAX_K) return GM_EINVAL;
+  if (n == 0) return GM_OK;
+  if (!ids || !R || !ctab_scratch || !out || !jout || !screened) return GM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
+  gm::diag_ctab_kernel<<<(k + 255) / 256, 256, 0, st>>>(ctab_scratch, k);
+  gm::diag_arrival_cost_kernel<<<gm::grid_for(n), 256, 0, st>>>(ids, R, n, k, k0, k1, ctab_scratch, out, jout);
+  gm::diag_screen_cost_kernel<<<gm::grid_for(n), 256, 0, st>>>(ids, R, n, k, k0, k1, T, screened);
   return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
 }

@@ -9,8 +9,9 @@ namespace gm {
 
 // arrivals, elements, screened, warp-path elements, escalated passes, CAS retries, then the
 // summed per-warp clocks of the light, 8-lane, 32-lane, dense phases, barrier waits, row setup,
-// row finish and the total
-constexpr int WS_NCOUNTERS = 14;
+// row finish and the total, then the kept arrivals (those within the bound) and the short rows
+// whose first-pass bound was below y*
+constexpr int WS_NCOUNTERS = 16;
 constexpr uint32_t WS_EDATA = 1u;
 constexpr uint32_t WS_ETIMEOUT = 2u;
 constexpr int SPLIT_LEN = 32768;  // rows longer than this are cut into chunks of this many elements
@@ -88,6 +89,13 @@ constexpr size_t ws_bytes(int32_t n_rows, int64_t nnz, int k) {
          round_up((size_t)n_rows * 4, 256) + round_up((size_t)max_long_rows(nnz) * sizeof(LongRow), 256) +
          round_up((size_t)max_long_rows(nnz) * (size_t)k * 16, 256) + round_up((size_t)max_long_rows(nnz) * 4, 256);
 }
+
+// The sketch launcher behind gm_sketch, gm_sketch_plain, gm_sketch_noalloc and
+// gm_sketch_learned.  t_row: per-row first-pass bounds (device floats) or null
+// for the closed-form bound.
+int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
+                  int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
+                  size_t workspace_bytes, cudaStream_t stream, bool plain, const float* t_row);
 
 // Entries per dense permutation: k rounded up to a multiple of 8, so that each
 // array starts on a 16-byte boundary (16-byte stores).

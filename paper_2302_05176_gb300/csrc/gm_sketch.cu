@@ -55,8 +55,8 @@ constexpr uint32_t TAG_MASK = 3u << 30, SLOT_MASK = (1u << 30) - 1u;
 
 // Per-thread counters (the per-warp phase clocks live in shared memory).
 struct Counters {
-  uint32_t arrivals, elements, screened, heavy, escalated, cas;
-  __device__ void zero() { arrivals = elements = screened = heavy = escalated = cas = 0u; }
+  uint32_t arrivals, elements, screened, heavy, escalated, cas, kept, fallback;
+  __device__ void zero() { arrivals = elements = screened = heavy = escalated = cas = kept = fallback = 0u; }
 };
 constexpr int CLK_LIGHT = 0, CLK_MEDIUM = 1, CLK_HEAVY = 2, CLK_SUPER = 3, CLK_WAIT = 4, CLK_SETUP = 5,
               CLK_FINISH = 6, CLK_TOTAL = 7, NCLK = 8;
@@ -83,6 +83,7 @@ struct SketchArgs {
   int max_long;
   int ndense;             // dense permutations per CTA (warps that take super-heavy elements)
   float q1, q2, q_split;  // normalised bounds: first pass, later passes, long rows (inf = none)
+  const float* t_row;     // learned first-pass bound per row (absolute), or null
 };
 
 struct SmemScalars {
@@ -171,7 +172,10 @@ __device__ __forceinline__ void seg_phase(const SketchArgs& a, int64_t lo, uint6
     if (act && sl == 0) cnt.arrivals += (uint32_t)min(SW, k - z0);
     int c;
     fill += seg_fy_steps<SW>(pi, z0, J, nkeep, lane, c);
-    if (sl < nkeep) cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
+    if (sl < nkeep) {
+      cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
+      ++cnt.kept;
+    }
     z0 += SW;
     if (act) {
       if (nkeep < SW || z0 >= k) {
@@ -312,6 +316,7 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
       continue;
     }
     cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
+    ++cnt.kept;
     if (++z >= k) e = -1;
   }
 }
@@ -456,13 +461,14 @@ __device__ __forceinline__ void block_sum(const SketchArgs& a, int64_t lo, int n
 
 __device__ __forceinline__ void flush_counters(const SketchArgs& a, Counters& cnt, bool gave_up) {
   const int lane = threadIdx.x & 31;
-  const uint32_t v32[6] = {cnt.arrivals, cnt.elements, cnt.screened, cnt.heavy, cnt.escalated, cnt.cas};
+  const uint32_t v32[8] = {cnt.arrivals, cnt.elements, cnt.screened, cnt.heavy,
+                           cnt.escalated, cnt.cas, cnt.kept, cnt.fallback};
 #pragma unroll
-  for (int q = 0; q < 6; ++q) {
+  for (int q = 0; q < 8; ++q) {
     unsigned long long v = v32[q];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
-    if (lane == 0 && v) atomicAdd(&a.hdr->counters[q], v);
+    if (lane == 0 && v) atomicAdd(&a.hdr->counters[q < 6 ? q : 6 + NCLK + (q - 6)], v);
   }
   if (lane == 0)
     for (int q = 0; q < NCLK; ++q)
@@ -530,7 +536,7 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
   block_sum<BLOCK>(a, lo, n, sh.red_f, sh.red_i, sumv, npos);
   clk_add(cnt, CLK_SETUP, t);
   for (int pass = first_pass; npos > 0; ++pass) {
-    float Tf = (pass == 0 ? a.q1 : a.q2) / sumv;
+    float Tf = pass == 0 ? (a.t_row ? __ldg(&a.t_row[row]) : a.q1 / sumv) : a.q2 / sumv;
     double Td = 0.0;
     bool last = !(Tf < 3.0e38f) || pass >= 12;
     if (!last) {
@@ -556,7 +562,10 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
     const bool again = __syncthreads_or(empty) && !last;
     clk_add(cnt, CLK_FINISH, t);
     if (!again) break;
-    if (tid == 0) ++cnt.escalated;
+    if (tid == 0) {
+      ++cnt.escalated;
+      if (pass == 0) ++cnt.fallback;
+    }
   }
   write_out(a, row, regs);
   clk_add(cnt, CLK_FINISH, t);
@@ -635,7 +644,7 @@ __global__ void __launch_bounds__(BLOCK, 2) fastgm_kernel(SketchArgs a) {
     const int64_t chi = min(hi, clo + SPLIT_LEN);
     const LongRow lr = a.longs[longi];
     if (lr.npos > 0 && chi > clo) {
-      float Tf = a.q_split / lr.sum;
+      float Tf = a.t_row ? __ldg(&a.t_row[row]) : a.q_split / lr.sum;
       const bool none = !(Tf < 3.0e38f);
       const uint64_t Tbits = none ? DBL_MAX_BITS : (uint64_t)__double_as_longlong(f64_from_f32(Tf));
       if (none) Tf = __int_as_float(0x7F800000);
@@ -721,7 +730,10 @@ __global__ void __launch_bounds__(BLOCK, 1) plain_kernel(SketchArgs a) {
         const int nz = min(32, k - z0);
         if (lane == 0) cnt.arrivals += (uint32_t)nz;
         warp_fy_steps(dp, z0, J, nz, lane, c);
-        if (lane < nz && bb <= DBL_MAX_BITS) cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
+        if (lane < nz && bb <= DBL_MAX_BITS) {
+          cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
+          ++cnt.kept;
+        }
       }
     }
     __syncthreads();
@@ -883,6 +895,10 @@ static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
   return GM_OK;
 }
 
+// Optional events recorded around the main FastGM (or plain) kernel launch, for
+// timing that kernel alone on the call's stream (gm_diag_time_main_kernel).
+static cudaEvent_t g_main_before = nullptr, g_main_after = nullptr;
+
 template <int ARITH>
 static int launch_all(const SketchArgs& a, bool plain, int nsm, cudaStream_t stream) {
   const size_t sm = plain ? plain_smem_bytes(a.k) : fast_smem_bytes(a.k, a.ndense);
@@ -893,12 +909,16 @@ static int launch_all(const SketchArgs& a, bool plain, int nsm, cudaStream_t str
   if (plain) {
     rc = occupancy_grid(plain_kernel<ARITH>, sm, nsm, max_units, grid);
     if (rc != GM_OK) return rc;
+    if (g_main_before) cudaEventRecord(g_main_before, stream);
     plain_kernel<ARITH><<<grid, BLOCK, sm, stream>>>(a);
+    if (g_main_after) cudaEventRecord(g_main_after, stream);
     return GM_OK;
   }
   rc = occupancy_grid(fastgm_kernel<ARITH, MODE_MAIN>, sm, nsm, max_units, grid);
   if (rc != GM_OK) return rc;
+  if (g_main_before) cudaEventRecord(g_main_before, stream);
   fastgm_kernel<ARITH, MODE_MAIN><<<grid, BLOCK, sm, stream>>>(a);
+  if (g_main_after) cudaEventRecord(g_main_after, stream);
   int grid_esc = 0;
   rc = occupancy_grid(fastgm_kernel<ARITH, MODE_ESC>, sm, nsm, a.max_long, grid_esc);
   if (rc != GM_OK) return rc;
@@ -908,7 +928,7 @@ static int launch_all(const SketchArgs& a, bool plain, int nsm, cudaStream_t str
 
 int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
                   int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
-                  size_t workspace_bytes, cudaStream_t stream, bool plain) {
+                  size_t workspace_bytes, cudaStream_t stream, bool plain, const float* t_row) {
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K) return GM_EINVAL;
   if (nnz > 0x7FFFFFFFll) return GM_EINVAL;
   if (!workspace || !row_ptr || (n_rows > 0 && (!s_out || !y_out)) || (nnz > 0 && (!ids || !w)))
@@ -945,6 +965,7 @@ int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, i
   a.long_regs = reinterpret_cast<Reg*>(L.long_regs);
   a.esc = L.esc;
   a.max_long = (int)L.max_long;
+  a.t_row = plain ? nullptr : t_row;
   if (bound == GM_BOUND_NONE) {
     a.q1 = a.q2 = a.q_split = INFINITY;
   } else {
@@ -970,6 +991,13 @@ int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, i
 
 }  // namespace gm
 
+extern "C" int gm_diag_time_main_kernel(void* before, void* after) {
+  if ((before == nullptr) != (after == nullptr)) return GM_EINVAL;
+  gm::g_main_before = (cudaEvent_t)before;
+  gm::g_main_after = (cudaEvent_t)after;
+  return GM_OK;
+}
+
 extern "C" size_t gm_sketch_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k, uint32_t flags) {
   (void)flags;
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K) return 0;
@@ -980,14 +1008,14 @@ extern "C" int gm_sketch(const int64_t* row_ptr, const int32_t* ids, const doubl
                          int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
                          size_t workspace_bytes, void* stream) {
   return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags, s_out, y_out, workspace, workspace_bytes,
-                           (cudaStream_t)stream, false);
+                           (cudaStream_t)stream, false, nullptr);
 }
 
 extern "C" int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
                                int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out,
                                double* y_out, void* workspace, size_t workspace_bytes, void* stream) {
   return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags & (GM_FLAG_VALIDATE | GM_FLAG_FP64_UNIT),
-                           s_out, y_out, workspace, workspace_bytes, (cudaStream_t)stream, true);
+                           s_out, y_out, workspace, workspace_bytes, (cudaStream_t)stream, true, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1049,5 +1077,5 @@ extern "C" int gm_sketch_noalloc(const int64_t* row_ptr, const int32_t* ids, con
   // counters) and rewrites the 1/(k-z) table; the heavy list is written before it
   // is read.  No other state carries over from the previous call.
   return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags, s_out, y_out, scratch,
-                           gm::NOALLOC_SCRATCH_BYTES, (cudaStream_t)stream, false);
+                           gm::NOALLOC_SCRATCH_BYTES, (cudaStream_t)stream, false, nullptr);
 }

@@ -21,6 +21,9 @@ GM_BOUND_CLOSED = 0 << 4
 GM_BOUND_NONE = 1 << 4
 GM_BOUND_LEARNED = 2 << 4
 GM_MAX_K = 4096
+GM_MODEL_FEATURES = 8
+GM_MODEL_HIDDEN = 64
+GM_MODEL_PARAMS = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
 
 
 class GmError(RuntimeError):
@@ -36,7 +39,9 @@ class gm_stats(ctypes.Structure):
                 ("cycles_medium", ctypes.c_uint64), ("cycles_heavy", ctypes.c_uint64),
                 ("cycles_dense", ctypes.c_uint64), ("cycles_wait", ctypes.c_uint64),
                 ("cycles_setup", ctypes.c_uint64), ("cycles_finish", ctypes.c_uint64),
-                ("cycles_total", ctypes.c_uint64), ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("cycles_total", ctypes.c_uint64), ("kept", ctypes.c_uint64), ("rows_fallback", ctypes.c_uint64),
+                ("status", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
@@ -63,6 +68,20 @@ def lib():
         L.gm_jaccard.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp]
         L.gm_cardinality.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
         L.gm_merge.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]
+        L.gm_features.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp, _vp]
+        L.gm_row_ln_ystar.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
+        L.gm_model_init.argtypes = [_vp, ctypes.c_uint64, _vp]
+        L.gm_model_forward.argtypes = [_vp, _vp, ctypes.c_int32, _vp, _vp]
+        L.gm_model_grad_workspace_bytes.restype = ctypes.c_size_t
+        L.gm_model_grad.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_float, _vp, _vp, _vp, ctypes.c_size_t,
+                                    _vp]
+        L.gm_model_adam.argtypes = [_vp, _vp, _vp, ctypes.c_float, ctypes.c_int32, _vp]
+        L.gm_model_save.argtypes = [_vp, ctypes.c_char_p, _vp]
+        L.gm_model_load.argtypes = [_vp, ctypes.c_char_p, _vp]
+        L.gm_sketch_learned_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
+        L.gm_sketch_learned_workspace_bytes.restype = ctypes.c_size_t
+        L.gm_sketch_learned.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.c_uint32, _vp, ctypes.c_float, _vp, _vp, _vp, ctypes.c_size_t, _vp]
         L.gm_strerror.argtypes = [ctypes.c_int]
         L.gm_strerror.restype = ctypes.c_char_p
         L.gm_version.restype = ctypes.c_char_p
@@ -188,3 +207,112 @@ def to_device(csr, device="cuda"):
     """Copy a workloads.CSR to device tensors (row_ptr, ids, w)."""
     return (torch.from_numpy(csr.row_ptr).to(device), torch.from_numpy(csr.ids).to(device),
             torch.from_numpy(csr.w).to(device))
+
+
+# --- learned first-pass bound (gm_features / gm_model_* / gm_sketch_learned) ----------------------
+
+def gm_features(row_ptr, ids, w, k, out=None, stream=None):
+    """Per-row features [n_rows, 8] float32 (ln n+, ln sum v, ln max v, 4 quantiles, ln k)."""
+    _need_cuda(row_ptr, torch.int64, "row_ptr")
+    _need_cuda(w, torch.float64, "w")
+    n_rows = row_ptr.numel() - 1
+    if out is None:
+        out = torch.empty((n_rows, GM_MODEL_FEATURES), dtype=torch.float32, device=row_ptr.device)
+    _need_cuda(out, torch.float32, "out")
+    _check(lib().gm_features(_ptr(row_ptr), _ptr(ids), _ptr(w), n_rows, w.numel(), int(k), _ptr(out),
+                             _stream_handle(stream)), "gm_features")
+    return out
+
+
+def gm_row_ln_ystar(y, out=None, stream=None):
+    """ln max_j y[r, j] per row (float32; +inf where a register is unfilled)."""
+    _need_cuda(y, torch.float64, "y")
+    n, k = y.shape
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=y.device)
+    _check(lib().gm_row_ln_ystar(_ptr(y), n, k, _ptr(out), _stream_handle(stream)), "gm_row_ln_ystar")
+    return out
+
+
+def gm_model_init(seed, params=None, device=None, stream=None):
+    if params is None:
+        params = torch.empty(GM_MODEL_PARAMS, dtype=torch.float32, device=device or torch.device("cuda"))
+    _need_cuda(params, torch.float32, "params")
+    _check(lib().gm_model_init(_ptr(params), int(seed) & 0xFFFFFFFFFFFFFFFF, _stream_handle(stream)),
+           "gm_model_init")
+    return params
+
+
+def gm_model_forward(params, feats, out=None, stream=None):
+    _need_cuda(params, torch.float32, "params")
+    _need_cuda(feats, torch.float32, "feats")
+    n = feats.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=feats.device)
+    _check(lib().gm_model_forward(_ptr(params), _ptr(feats), n, _ptr(out), _stream_handle(stream)),
+           "gm_model_forward")
+    return out
+
+
+def gm_model_grad_workspace_bytes():
+    return int(lib().gm_model_grad_workspace_bytes())
+
+
+def gm_model_grad(params, feats, target, tau, grad=None, loss=None, ws=None, stream=None):
+    """Gradient of the mean pinball loss (level tau) -> (grad [P] f32, loss [1] f32, workspace)."""
+    _need_cuda(params, torch.float32, "params")
+    _need_cuda(feats, torch.float32, "feats")
+    _need_cuda(target, torch.float32, "target")
+    dev = params.device
+    grad = torch.empty(GM_MODEL_PARAMS, dtype=torch.float32, device=dev) if grad is None else grad
+    loss = torch.empty(1, dtype=torch.float32, device=dev) if loss is None else loss
+    if ws is None:
+        ws = torch.empty(gm_model_grad_workspace_bytes(), dtype=torch.uint8, device=dev)
+    _check(lib().gm_model_grad(_ptr(params), _ptr(feats), _ptr(target), target.numel(), float(tau), _ptr(grad),
+                               _ptr(loss), _ptr(ws), ws.numel(), _stream_handle(stream)), "gm_model_grad")
+    return grad, loss, ws
+
+
+def gm_model_adam(params, adam, grad, lr, step, stream=None):
+    _check(lib().gm_model_adam(_ptr(params), _ptr(adam), _ptr(grad), float(lr), int(step), _stream_handle(stream)),
+           "gm_model_adam")
+
+
+def gm_model_save(params, path, stream=None):
+    _check(lib().gm_model_save(_ptr(params), os.fsencode(path), _stream_handle(stream)), "gm_model_save")
+
+
+def gm_model_load(path, params=None, device=None, stream=None):
+    if params is None:
+        params = torch.empty(GM_MODEL_PARAMS, dtype=torch.float32, device=device or torch.device("cuda"))
+    _check(lib().gm_model_load(_ptr(params), os.fsencode(path), _stream_handle(stream)), "gm_model_load")
+    return params
+
+
+def sketch_learned_workspace_bytes(n_rows, nnz, k):
+    n = lib().gm_sketch_learned_workspace_bytes(int(n_rows), int(nnz), int(k))
+    if n == 0:
+        raise GmError(GM_EINVAL, "gm_sketch_learned_workspace_bytes")
+    return n
+
+
+def gm_sketch_learned(row_ptr, ids, w, k, seed, params, margin=0.0, flags=0, s_out=None, y_out=None, ws=None,
+                      stream=None):
+    """FastGM with a learned first-pass bound per row; the same registers as gm_sketch."""
+    _need_cuda(row_ptr, torch.int64, "row_ptr")
+    _need_cuda(ids, torch.int32, "ids")
+    _need_cuda(w, torch.float64, "w")
+    _need_cuda(params, torch.float32, "params")
+    n_rows, nnz = row_ptr.numel() - 1, ids.numel()
+    if w.numel() != nnz:
+        raise ValueError("ids and w differ in length")
+    dev = row_ptr.device
+    s_out = torch.empty((n_rows, k), dtype=torch.int32, device=dev) if s_out is None else s_out
+    y_out = torch.empty((n_rows, k), dtype=torch.float64, device=dev) if y_out is None else y_out
+    if ws is None:
+        ws = torch.empty(sketch_learned_workspace_bytes(n_rows, nnz, k), dtype=torch.uint8, device=dev)
+    rc = lib().gm_sketch_learned(_ptr(row_ptr), _ptr(ids), _ptr(w), n_rows, nnz, int(k),
+                                 int(seed) & 0xFFFFFFFFFFFFFFFF, int(flags), _ptr(params), float(margin),
+                                 _ptr(s_out), _ptr(y_out), _ptr(ws), ws.numel(), _stream_handle(stream))
+    _check(rc, "gm_sketch_learned")
+    return s_out, y_out, ws

@@ -104,6 +104,31 @@ def lognormal_batch(seed=1, n_rows=4096, median=2000.0, sigma=1.0, lo=10, hi=200
     return from_rows(rows)
 
 
+def lognormal_batch_device(seed, n_rows=4096, median=2000.0, sigma=1.0, lo=10, hi=200_000, device="cuda"):
+    """The lognormal_batch distribution drawn on the device (torch's Philox
+    generator), for training sets of many thousands of rows.  Row lengths and
+    weights follow lognormal_batch; the ids of row r are the arithmetic
+    progression (a_r + i s_r) mod 2^24 with a random start a_r and a random odd
+    step s_r, so they are distinct within the row.  Returns device tensors
+    (row_ptr int64, ids int32, w float64)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    z = torch.randn(n_rows, generator=g, device=device, dtype=torch.float64)
+    lens = torch.exp(np.log(median) + sigma * z).round().clamp_(lo, hi).to(torch.int64)
+    row_ptr = torch.zeros(n_rows + 1, dtype=torch.int64, device=device)
+    torch.cumsum(lens, 0, out=row_ptr[1:])
+    nnz = int(row_ptr[-1].item())
+    row = torch.repeat_interleave(torch.arange(n_rows, device=device), lens, output_size=nnz)
+    pos = torch.arange(nnz, device=device, dtype=torch.int64) - row_ptr[row]
+    start = torch.randint(0, ID_SPACE, (n_rows,), generator=g, device=device, dtype=torch.int64)
+    step = torch.randint(0, ID_SPACE // 2, (n_rows,), generator=g, device=device, dtype=torch.int64) * 2 + 1
+    ids = ((start[row] + pos * step[row]) % ID_SPACE).to(torch.int32)
+    w = torch.empty(nnz, dtype=torch.float64, device=device).exponential_(1.0, generator=g)
+    return row_ptr, ids, w
+
+
 def pareto_weights(rng, n, alpha, x_min):
     return x_min * (1.0 + rng.pareto(alpha, size=n))
 
