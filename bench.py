@@ -44,7 +44,10 @@ def parse():
     ap.add_argument("--only", default="all", choices=["all", "fastgm"],
                     help="fastgm: time only the FastGM step (the case profiled with ncu)")
     ap.add_argument("--k", type=int, default=K_MAIN, help="k of the --only fastgm step")
+    ap.add_argument("--flags", type=int, default=0, help="gm_sketch flags of the --only fastgm step")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-bound ablation")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
+    ap.add_argument("--serve-requests", type=int, default=400, help="requests in the serving stream")
     ap.add_argument("--learned-rows", type=int, default=200_000, help="sketches in the bound network's training set")
     ap.add_argument("--learned-steps", type=int, default=400, help="Adam steps of the bound network")
     ap.add_argument("--arith", action="store_true",
@@ -135,14 +138,18 @@ LEARNED_TAU = 0.95
 TRAFFIC = {"src_sha": None, "bytes": None}
 
 
+MAIN_KERNEL_SOURCES = ("gm_sketch.cu", "gm_device.cuh", "gm_arith.cuh", "gm_stream.cuh", "gm_log_tables.h",
+                       "gm_internal.h")
+
+
 def kernel_source_sha():
+    """sha256 (16 hex digits) of the sources the main sketch kernel is compiled from."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2302_05176_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in MAIN_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 
@@ -323,11 +330,8 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        from paper_2302_05176_gb300 import dist as D
+        return D.max_over_ranks(x, dist, "cuda")
 
     def timed(call, k, steps, warmup, learned_ws=False):
         """Time `steps` calls (after `warmup`) with CUDA events on the launching stream;
@@ -364,10 +368,11 @@ def main():
         return lambda s_out, y_out, ws: fn(rp, ids, w, k, SEED, flags=flags, s_out=s_out, y_out=y_out, ws=ws)
 
     if args.only == "fastgm":
-        ms, kms, st, _, _ = timed(sketch_call(gm.gm_sketch, args.k), args.k, args.steps, args.warmup)
+        ms, kms, st, _, _ = timed(sketch_call(gm.gm_sketch, args.k, args.flags), args.k, args.steps, args.warmup)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": world * n_rows / (ms * 1e-3), "unit": "sketches/s",
-                              "ms_per_step": ms, "kernel_ms": kms, "only": "fastgm k=%d" % args.k, "stats": st}),
+                              "ms_per_step": ms, "kernel_ms": kms, "only": "fastgm k=%d flags=%d" % (args.k, args.flags),
+                              "stats": st}),
                   flush=True)
         return
     clocks = ClockSampler(local)
@@ -437,12 +442,81 @@ def main():
     if not args.no_learned:
         line["learned_k1024"] = learned_ablation(args, timed, sketch_call, (rp, ids, w), s_main, y_main, ms_main,
                                                  st_main, n_rows)
+    if not args.no_serve:
+        line["serving"] = serving_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(X, K_MAIN, SEED, n_rows=args.cpu_rows)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+SERVE_RATE = 20_000.0
+
+
+def serving_leg(args):
+    """Replay a Poisson stream of sketch / Jaccard / cardinality requests (20k req/s,
+    n+ log-uniform in [100, 5e6], Exp(1) / Pareto(1.5) weights, k in {256, 1024,
+    4096}) against the serving engine.  Each request is submitted at its arrival
+    time; its latency runs from that time to the engine's completion stamp."""
+    import torch
+    from paper_2302_05176_gb300 import server as S
+    from paper_2302_05176_gb300 import workloads as W
+    t0 = time.perf_counter()
+    reqs = W.serving_requests(seed=SEED, n_requests=args.serve_requests, rate=SERVE_RATE)
+    bufs = {i: (torch.from_numpy(r.csr.ids).pin_memory(), torch.from_numpy(r.csr.w).pin_memory())
+            for i, r in enumerate(reqs) if r.kind == "sketch"}  # a front end receives into page-locked memory
+    gen_s = time.perf_counter() - t0
+    with S.Server(seed=SEED, device_bytes=16 << 30, n_streams=2) as srv:
+        rng = np.random.default_rng(7)
+        warm = [srv.submit_sketch(rng.choice(1 << 24, 1000, replace=False).astype(np.int32),
+                                  rng.exponential(size=1000), k) for k in (256, 1024, 4096)]
+        for t in warm:
+            srv.wait(t, 60.0)
+        for t in warm:
+            srv.release(t)
+        tick, due = {}, {}
+        start = S.now_ns() + 1_000_000
+        for i, r in enumerate(reqs):
+            d = start + int(r.t_arrive * 1e9)
+            while S.now_ns() < d:
+                pass
+            if r.kind == "sketch":
+                tick[i] = srv.submit_sketch(bufs[i][0], bufs[i][1], r.k)
+            elif r.kind == "jaccard":
+                tick[i] = srv.submit_jaccard(tick[r.pair[0]], tick[r.pair[1]])
+            else:
+                tick[i] = srv.submit_cardinality(tick[r.handle])
+            due[i] = d
+        lat = {"sketch": [], "jaccard": [], "cardinality": []}
+        last = start
+        batch = []
+        for i, r in enumerate(reqs):
+            rc, res = srv.wait(tick[i], 600.0)
+            if rc != 0:
+                raise RuntimeError("serving request %d failed: %d" % (i, rc))
+            lat[r.kind].append((res["t_done_ns"] - due[i]) / 1e6)
+            last = max(last, res["t_done_ns"])
+            if r.kind == "sketch":
+                batch.append(res["batch_size"])
+        st = srv.stats()
+    span = (last - start) / 1e9
+    every = np.concatenate([np.asarray(v) for v in lat.values()])
+    nnz = sum(r.csr.nnz for r in reqs if r.kind == "sketch")
+    pct = lambda v, q: float(np.percentile(v, q)) if len(v) else None
+    return {"requests": len(reqs), "sketches": len(lat["sketch"]),
+            "queries": len(lat["jaccard"]) + len(lat["cardinality"]),
+            "offered_rate_rps": SERVE_RATE, "span_s": span, "throughput_rps": len(reqs) / span,
+            "elements_per_s": nnz / span, "elements": nnz,
+            "p50_ms": pct(every, 50), "p99_ms": pct(every, 99),
+            "sketch_p50_ms": pct(lat["sketch"], 50), "sketch_p99_ms": pct(lat["sketch"], 99),
+            "query_p50_ms": pct(lat["jaccard"] + lat["cardinality"], 50),
+            "query_p99_ms": pct(lat["jaccard"] + lat["cardinality"], 99),
+            "sketch_batches": st["sketch_batches"], "query_batches": st["query_batches"],
+            "mean_batch_rows": float(np.mean(batch)), "arena_peak_bytes": st["arena_peak_bytes"],
+            "input": "pinned host buffers, copied by the engine inside the measured latency",
+            "generate_s": gen_s}
 
 
 def learned_ablation(args, timed, sketch_call, dev_csr, s_main, y_main, ms_main, st_main, n_rows):

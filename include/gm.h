@@ -67,6 +67,10 @@ extern "C" {
  * Products and reciprocals are bit-identical either way; the two logarithms
  * differ by at most one ulp.  Slower on GB300; kept for comparison. */
 #define GM_FLAG_FP64_UNIT (1u << 2)
+/* Compute -ln(u) on the integer pipes but the two products of each arrival and
+ * 1/v on the FP64 unit (IEEE multiply and reciprocal: the same bits).  Same
+ * registers as the default; a throughput choice.  Ignored with GM_FLAG_FP64_UNIT. */
+#define GM_FLAG_FP64_PRODUCTS (1u << 1)
 /* Testing aid: divide the closed-form bounds of the first pass (and of long-row
  * chunks) by 8, so that most rows find a register unfilled and take the
  * escalation paths.  The registers are the same; only the work grows. */

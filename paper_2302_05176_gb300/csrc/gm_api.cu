@@ -5,6 +5,7 @@
 
 #include "gm.h"
 #include "gm_internal.h"
+#include "gm_server.h"
 
 extern "C" int gm_status(const void* workspace, gm_stats* stats, void* stream) {
   if (!workspace) return GM_EINVAL;
@@ -44,6 +45,8 @@ extern "C" const char* gm_strerror(int code) {
     case GM_ECUDA: return "CUDA error";
     case GM_ETIMEOUT: return "device retry limit reached";
     case GM_EDATA: return "invalid input data";
+    case GM_EAGAIN: return "not finished yet";
+    case GM_ECANCELED: return "cancelled";
     default: return "unknown status";
   }
 }

@@ -3,47 +3,27 @@
 #include <cuda_runtime.h>
 
 #include "gm.h"
+#include "gm_estim.cuh"
 
 namespace gm {
 
-constexpr int EST_BLOCK = 256;
-
-// One warp per pair: count equal, filled registers with ballots.
+// One warp per pair: count equal, filled registers.
 __global__ void jaccard_kernel(const int32_t* __restrict__ sa, const int32_t* __restrict__ sb, int64_t n_pairs,
                                int k, double* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
   for (int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); p < n_pairs; p += warps) {
-    const int32_t* a = sa + p * k;
-    const int32_t* b = sb + p * k;
-    int hits = 0;
-    for (int j = lane; j < k; j += 32) {
-      const int32_t x = a[j], y = b[j];
-      hits += (x >= 0 && x == y) ? 1 : 0;
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) hits += __shfl_xor_sync(0xFFFFFFFFu, hits, d);
-    if (lane == 0) out[p] = (double)hits / (double)k;
+    const double j = warp_jaccard(sa + p * k, sb + p * k, k);
+    if ((threadIdx.x & 31) == 0) out[p] = j;
   }
 }
 
 // One CTA per row: FP64 tree sum of the registers, then (k - 1) / sum.
-__global__ void cardinality_kernel(const double* __restrict__ y, int n_rows, int k, double* __restrict__ out) {
+__global__ void __launch_bounds__(EST_BLOCK) cardinality_kernel(const double* __restrict__ y, int n_rows, int k,
+                                                                double* __restrict__ out) {
   __shared__ double part[EST_BLOCK / 32];
   for (int r = blockIdx.x; r < n_rows; r += gridDim.x) {
-    const double* row = y + (int64_t)r * k;
-    double s = 0.0;
-    for (int j = threadIdx.x; j < k; j += blockDim.x) s += row[j];
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, d);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += part[q];
-      out[r] = (double)(k - 1) / t;  // an unfilled register (inf) gives 0
-    }
-    __syncthreads();
+    const double c = block_cardinality(y + (int64_t)r * k, k, part);
+    if (threadIdx.x == 0) out[r] = c;
   }
 }
 

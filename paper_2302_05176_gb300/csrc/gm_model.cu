@@ -148,7 +148,7 @@ __device__ __forceinline__ int weight_bin(uint64_t bits) {
 }
 
 struct FeatSmem {
-  int hist[NBINS];
+  int hist[NW][NBINS];  // one histogram per warp: fewer lanes contend for a bin
   int red_i[NW];
   double red_s[NW], red_m[NW];
   int scan[NW];
@@ -159,35 +159,46 @@ struct FeatSmem {
 __device__ void row_features(const double* __restrict__ w, int64_t lo, int64_t hi, int k, FeatSmem& sm,
                              float* feat) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int b = tid; b < NBINS; b += NT) sm.hist[b] = 0;
+  for (int b = tid; b < NW * NBINS; b += NT) (&sm.hist[0][0])[b] = 0;
   __syncthreads();
+  // Four loads in flight per thread.
+  constexpr int U = 4;
   int np = 0;
-  double sum = 0.0, mx = 0.0;
-  for (int64_t i = lo + tid; i < hi; i += NT) {
-    const double v = __ldg(&w[i]);
-    const uint64_t b = (uint64_t)__double_as_longlong(v);
-    if (b > 0ull && b < INF_BITS) {  // positive and finite
-      ++np;
-      sum += v;
-      mx = fmax(mx, v);
-      atomicAdd(&sm.hist[weight_bin(b) - BIN_MIN], 1);
+  double sum = 0.0;
+  uint64_t mxb = 0ull;  // positive doubles order like their bit patterns
+  for (int64_t base = lo + (tid - lane); base < hi; base += (int64_t)U * NT) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * NT + lane;
+      v[u] = i < hi ? __ldg(&w[i]) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t b = (uint64_t)__double_as_longlong(v[u]);
+      const bool ok = b > 0ull && b < INF_BITS;  // positive and finite
+      np += ok ? 1 : 0;
+      sum += ok ? v[u] : 0.0;
+      mxb = (ok && b > mxb) ? b : mxb;
+      if (ok) atomicAdd(&sm.hist[warp][weight_bin(b) - BIN_MIN], 1);
     }
   }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
     np += __shfl_xor_sync(FULL, np, d);
     sum += __shfl_xor_sync(FULL, sum, d);
-    mx = fmax(mx, __shfl_xor_sync(FULL, mx, d));
+    const uint64_t o = __shfl_xor_sync(FULL, mxb, d);
+    mxb = o > mxb ? o : mxb;
   }
   if (lane == 0) {
     sm.red_i[warp] = np;
     sm.red_s[warp] = sum;
-    sm.red_m[warp] = mx;
+    sm.red_m[warp] = __longlong_as_double((long long)mxb);
   }
   __syncthreads();
   np = 0;
   sum = 0.0;
-  mx = 0.0;
+  double mx = 0.0;
   for (int q = 0; q < NW; ++q) {
     np += sm.red_i[q];
     sum += sm.red_s[q];
@@ -195,9 +206,15 @@ __device__ void row_features(const double* __restrict__ w, int64_t lo, int64_t h
   }
   // exclusive scan of the histogram: thread t owns bins 4t .. 4t+3
   static_assert(NBINS == 4 * NT, "four bins per thread");
-  int own = 0;
+  int cnt4[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) own += sm.hist[4 * tid + q];
+  for (int q = 0; q < 4; ++q) {
+    int c = 0;
+#pragma unroll
+    for (int w8 = 0; w8 < NW; ++w8) c += sm.hist[w8][4 * tid + q];
+    cnt4[q] = c;
+  }
+  const int own = cnt4[0] + cnt4[1] + cnt4[2] + cnt4[3];
   int incl = own;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -216,7 +233,7 @@ __device__ void row_features(const double* __restrict__ w, int64_t lo, int64_t h
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int before = c;
-      c += sm.hist[4 * tid + q];
+      c += cnt4[q];
       if (np > 0 && before < r && c >= r) sm.qbin[qi] = BIN_MIN + 4 * tid + q;
     }
   }

@@ -90,6 +90,7 @@ struct SmemScalars {
   int pool, hcount, pcount, c_med, c_heavy, c_pheavy, c_super, c_psuper, unit, last;
   float red_f[WARPS];
   int red_i[WARPS];
+  unsigned long long red_u[WARPS];
   unsigned long long clk[WARPS][NCLK];  // light, 8-lane, 32-lane, dense, barrier wait, setup, finish, total
 };
 __shared__ SmemScalars sh_scalars;
@@ -334,14 +335,41 @@ __device__ __forceinline__ void clk_add(Counters&, int which, long long& t) {
   t = now;
 }
 
+// FastPrune's bound, refreshed lazily (Sec. 2.2): once every register is filled,
+// the largest register y* bounds every arrival that can still lower a register,
+// so min(T, y*) replaces T.  Registers only decrease, so a y* read at a phase
+// boundary stays valid for the rest of the pass.  Block-wide (two barriers).
+__device__ __forceinline__ uint64_t refresh_bound(const Reg* regs, int k, uint64_t Tbits, SmemScalars& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long m = 0ull;
+  for (int j = threadIdx.x; j < k; j += BLOCK) {
+    const unsigned long long y = regs[j].y;  // an unfilled register is +inf, above every bound
+    m = y > m ? y : m;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(FULL, m, d);
+    m = o > m ? o : m;
+  }
+  if (lane == 0) sh.red_u[warp] = m;
+  __syncthreads();
+  unsigned long long t = 0ull;
+#pragma unroll
+  for (int q = 0; q < WARPS; ++q) t = sh.red_u[q] > t ? sh.red_u[q] : t;
+  __syncthreads();
+  return t < Tbits ? t : Tbits;
+}
+
 // All warp-path classes of one pass, in order: 8-lane segments, 32-lane warps
-// (work list, then promotions), dense permutations (warps < ndense).
+// (work list, then promotions), dense permutations (warps < ndense); the bound
+// is refreshed from y* before each class.
 template <int ARITH>
 __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uint64_t Tbits, Reg* regs,
                                             uint32_t* area, uint16_t* dense, SmemScalars& sh, Counters& cnt,
                                             bool& gave_up, long long& t) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nh = sh.hcount;
+  Tbits = refresh_bound(regs, a.k, Tbits, sh);
   {
     const int seg = lane / MED_SW;
     const HashPiN<MED_SLOTS> hp{area + (warp * (32 / MED_SW) + seg) * MED_SLOTS};
@@ -350,6 +378,7 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uin
   }
   clk_add(cnt, CLK_MEDIUM, t);
   __syncthreads();
+  Tbits = refresh_bound(regs, a.k, Tbits, sh);
   clk_add(cnt, CLK_WAIT, t);
   {
     const HashPi hp{area + warp * HASH_SLOTS};
@@ -360,6 +389,7 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uin
   }
   clk_add(cnt, CLK_HEAVY, t);
   __syncthreads();
+  Tbits = refresh_bound(regs, a.k, Tbits, sh);
   clk_add(cnt, CLK_WAIT, t);
   // dense permutations: the CTA's own, then as many as fit in the (now idle) hash area
   const int ndense = min(WARPS, a.ndense + (int)(fast_area_bytes() / (pi_stride(a.k) * 2)));
@@ -846,8 +876,11 @@ __global__ void __launch_bounds__(256) longprep_kernel(SketchArgs a) {
     a.long_regs[j].y = INF_BITS;
     a.long_regs[j].id = UNFILLED_ID;
   }
-  for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+  // SUB pieces per chunk, so that enough CTAs stream each long row
+  constexpr int SUB = 8, PIECE = SPLIT_LEN / SUB;
+  for (uint32_t cs = blockIdx.x; cs < n_chunks * SUB; cs += gridDim.x) {
     // chunk c: the first chunk of long row c (c < n_long) or extra unit c - n_long
+    const uint32_t c = cs / SUB, piece = cs % SUB;
     int row, chunk, longi;
     if (c < n_long) {
       longi = (int)c;
@@ -858,7 +891,9 @@ __global__ void __launch_bounds__(256) longprep_kernel(SketchArgs a) {
     }
     int64_t lo, hi;
     row_bounds(a, row, lo, hi);
-    const int64_t clo = lo + (int64_t)chunk * SPLIT_LEN, chi = min(hi, clo + SPLIT_LEN);
+    const int64_t clo = lo + (int64_t)chunk * SPLIT_LEN + (int64_t)piece * PIECE;
+    const int64_t chi = min(hi, clo + PIECE);
+    if (chi <= clo) continue;  // uniform over the block
     float s;
     int np;
     block_sum<256>(a, clo, (int)(chi - clo), red_f, red_i, s, np);
@@ -983,8 +1018,9 @@ int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, i
   if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
     return GM_ECUDA;
   a.ndense = dense_buffers(k, (size_t)smem_sm);
-  const int rc = (flags & GM_FLAG_FP64_UNIT) ? launch_all<ARITH_FP64>(a, plain, nsm, stream)
-                                             : launch_all<ARITH_INT>(a, plain, nsm, stream);
+  const int rc = (flags & GM_FLAG_FP64_UNIT)       ? launch_all<ARITH_FP64>(a, plain, nsm, stream)
+                 : (flags & GM_FLAG_FP64_PRODUCTS) ? launch_all<ARITH_MIX>(a, plain, nsm, stream)
+                                                   : launch_all<ARITH_INT>(a, plain, nsm, stream);
   if (rc != GM_OK) return rc;
   return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
 }
@@ -1014,7 +1050,7 @@ extern "C" int gm_sketch(const int64_t* row_ptr, const int32_t* ids, const doubl
 extern "C" int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
                                int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out,
                                double* y_out, void* workspace, size_t workspace_bytes, void* stream) {
-  return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags & (GM_FLAG_VALIDATE | GM_FLAG_FP64_UNIT),
+  return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags & (GM_FLAG_VALIDATE | GM_FLAG_FP64_UNIT | GM_FLAG_FP64_PRODUCTS),
                            s_out, y_out, workspace, workspace_bytes, (cudaStream_t)stream, true, nullptr);
 }
 

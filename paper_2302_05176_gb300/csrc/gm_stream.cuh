@@ -11,14 +11,17 @@ namespace gm {
 
 // Arithmetic of an arrival: ARITH_INT computes -ln u, the products and 1/v on the
 // integer pipes (gm_arith.cuh); ARITH_FP64 uses the FP64 unit (CUDA's log and the
-// IEEE product / reciprocal), kept for comparison.  Products and reciprocals are
-// bit-identical between the two; the logarithms differ by at most an ulp.
+// IEEE product / reciprocal), kept for comparison; ARITH_MIX takes -ln u from the
+// integer pipes and the products and 1/v from the FP64 unit, which is otherwise
+// idle.  Products and reciprocals are bit-identical in all three; the logarithms
+// of ARITH_FP64 differ from the other two by at most an ulp.
 constexpr int ARITH_FP64 = 0;
 constexpr int ARITH_INT = 1;
+constexpr int ARITH_MIX = 2;
 
 template <int ARITH>
 __device__ __forceinline__ double arr_neglog(const Words& wd) {
-  if constexpr (ARITH == ARITH_INT)
+  if constexpr (ARITH != ARITH_FP64)
     return neglog_u(wd.w0, wd.w1);
   else
     return -log(uniform_open(wd.w0, wd.w1));

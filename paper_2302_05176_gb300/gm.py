@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libgm.so")
 GM_OK, GM_EINVAL, GM_ENOMEM, GM_ECUDA, GM_ETIMEOUT, GM_EDATA = 0, 1, 2, 3, 4, 5
 GM_FLAG_VALIDATE = 1 << 0
 GM_FLAG_FP64_UNIT = 1 << 2
+GM_FLAG_FP64_PRODUCTS = 1 << 1
 GM_FLAG_TIGHT_BOUND = 1 << 3
 GM_BOUND_CLOSED = 0 << 4
 GM_BOUND_NONE = 1 << 4

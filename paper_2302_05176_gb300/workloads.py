@@ -187,33 +187,66 @@ class Request:
     handle: int = -1     # for cardinality
 
 
+def _progression_ids(rng, n, space=ID_SPACE):
+    """n distinct ids in [0, space): (a + i s) mod space with a random start and a
+    random odd step (space a power of two).  O(n), for large request streams; the
+    sketch keys its random numbers on the id, so the structure is immaterial."""
+    a = int(rng.integers(0, space))
+    st = int(rng.integers(0, space // 2)) * 2 + 1
+    return ((a + np.arange(n, dtype=np.int64) * st) % space).astype(np.int32)
+
+
 def serving_requests(seed=1, n_requests=2000, rate=20_000.0, n_lo=100, n_hi=5_000_000,
-                     ks=(256, 1024, 4096), query_frac=0.3, max_nnz=None):
+                     ks=(256, 1024, 4096), query_frac=0.3, pair_frac=0.5, shared=0.5, sigma=0.2,
+                     max_nnz=None):
     """A Poisson stream of sketch requests plus Jaccard / cardinality queries.
 
-    Queries refer to earlier sketch requests by their index in the stream.
-    ``max_nnz`` caps n+ (used by tests to keep the case small).
+    Sketch sizes n+ are log-uniform in [n_lo, n_hi], weights Exp(1) or
+    Pareto(1.5) (an equal mixture), k uniform over ``ks``.  A fraction
+    ``pair_frac`` of the sketch requests are partners of an earlier request: they
+    keep ``shared`` of its ids with the weights multiplied by exp(N(0, sigma^2)),
+    add fresh ids for the rest, and use its k; the Jaccard queries are over such
+    pairs, the cardinality queries over any earlier sketch.  Queries refer to
+    sketch requests by their index in the stream.  ``max_nnz`` caps n+.
     """
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
     hi = n_hi if max_nnz is None else min(n_hi, max_nnz)
-    reqs = []
-    sketch_idx = []
+    reqs, sketch_idx, pairs = [], [], []
     for q in range(n_requests):
         if sketch_idx and rng.random() < query_frac:
-            if rng.random() < 0.5 and len(sketch_idx) >= 2:
-                a, b = rng.choice(sketch_idx, size=2, replace=False)
-                reqs.append(Request(float(t[q]), "jaccard", 0, pair=(int(a), int(b))))
+            if pairs and rng.random() < 0.5:
+                a, b = pairs[int(rng.integers(len(pairs)))]
+                reqs.append(Request(float(t[q]), "jaccard", reqs[a].k, pair=(a, b)))
             else:
-                reqs.append(Request(float(t[q]), "cardinality", 0, handle=int(rng.choice(sketch_idx))))
+                h = int(rng.choice(sketch_idx))
+                reqs.append(Request(float(t[q]), "cardinality", reqs[h].k, handle=h))
+            continue
+        if sketch_idx and rng.random() < pair_frac:
+            a = int(rng.choice(sketch_idx))
+            base = reqs[a].csr
+            n = base.nnz
+            keep = rng.random(n) < shared
+            n_fresh = n - int(keep.sum())
+            # fresh ids from a block of their own above the base ids' range, so
+            # they never repeat a kept id (blocks of 2^23 ids, reused cyclically)
+            block = 2 + len(pairs) % 254
+            fresh = (block << 23) + _progression_ids(rng, n_fresh, 1 << 23).astype(np.int64)
+            ids = np.concatenate([base.ids[keep].astype(np.int64), fresh])
+            w = np.concatenate([base.w[keep] * np.exp(rng.normal(0.0, sigma, n - n_fresh)),
+                                rng.standard_exponential(n_fresh)])
+            if len(pairs) >= 254:  # a reused block may meet a partner's kept ids
+                ids, first = np.unique(ids, return_index=True)
+                w = w[first]
+            reqs.append(Request(float(t[q]), "sketch", reqs[a].k, csr=CSR(np.array([0, ids.size], dtype=np.int64),
+                                                                       ids.astype(np.int32), w)))
+            pairs.append((a, q))
+            sketch_idx.append(q)
             continue
         n = int(np.exp(rng.uniform(np.log(n_lo), np.log(hi))))
-        ids = _distinct_ids(rng, n, ID_SPACE)
-        if rng.random() < 0.5:
-            w = rng.standard_exponential(n)
-        else:
-            w = pareto_weights(rng, n, 1.5, 1.0)
+        ids = _progression_ids(rng, n)
+        w = rng.standard_exponential(n) if rng.random() < 0.5 else pareto_weights(rng, n, 1.5, 1.0)
         k = int(rng.choice(ks))
-        reqs.append(Request(float(t[q]), "sketch", k, csr=from_rows([(ids, w)])))
+        reqs.append(Request(float(t[q]), "sketch", k, csr=CSR(np.array([0, n], dtype=np.int64), ids, w)))
         sketch_idx.append(q)
     return reqs
