@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--flags", type=int, default=0, help="gm_sketch flags of the --only fastgm step")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-bound ablation")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
+    ap.add_argument("--no-tune", action="store_true", help="time the default tuning instead of gm_tune's")
+    ap.add_argument("--tuning-file", default=None, help="load the tuning table from this file if it exists, "
+                    "else tune and save it there")
     ap.add_argument("--serve-requests", type=int, default=400, help="requests in the serving stream")
     ap.add_argument("--learned-rows", type=int, default=200_000, help="sketches in the bound network's training set")
     ap.add_argument("--learned-steps", type=int, default=400, help="Adam steps of the bound network")
@@ -124,11 +127,12 @@ class ClockSampler:
 
 
 # Work units of the sketch kernel and their cost in lane-instructions, counted by
-# ncu (smsp__thread_inst_executed.sum) on gm_diag_arrival_cost's two kernels, which
-# run one arrival (Philox, -ln u, RN(E C_z), the exact sum, RN(S R), RandInt) and
-# one first-arrival screen per thread over 2^24 elements: 7,373,606,055 and
-# 1,477,443,584 lane-instructions.
-LANE_INST_PER_ARRIVAL = 7373606055 / 2 ** 24   # 439.5
+# ncu (smsp__thread_inst_executed.sum) on gm_diag_arrival_cost's kernels, which run
+# one arrival (Philox, -ln u, RN(E C_z), the exact sum, RN(S R), RandInt) and one
+# first-arrival screen per thread over 2^24 elements: the arrival in the default
+# arithmetic (integer-pipe log, FP64-unit products) took 5,847,328,614, the screen
+# 1,477,443,584 (the all-integer arrival 7,373,606,055).
+LANE_INST_PER_ARRIVAL = 5847328614 / 2 ** 24   # 348.5
 LANE_INST_PER_SCREEN = 1477443584 / 2 ** 24    # 88.1
 LANES_PER_SM = 128                              # 4 sub-partitions x 32 lanes issue per clock
 LAUNCHES_PER_CALL = 5                           # init, plan, long-row prep, main, long-row redo
@@ -165,7 +169,7 @@ def alu_roofline(st, kernel_ms):
     achieved = work / (kernel_ms * 1e-3) / 1e12
     traffic = TRAFFIC["bytes"] if TRAFFIC["src_sha"] == kernel_source_sha() else None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-inst/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "fastgm_kernel<1, 0>", "kernel_ms": kernel_ms,
+            "traffic": traffic, "kernel": "fastgm_kernel<2, 0>", "kernel_ms": kernel_ms,
             "peak_source": "derived: %d SMs x %d lanes x %.0f MHz" % (props.multi_processor_count, LANES_PER_SM, mhz),
             "work_lane_inst": work, "kept_arrivals": st["kept"], "screened_elements": st["elements"]}
 
@@ -367,12 +371,25 @@ def main():
     def sketch_call(fn, k, flags=0):
         return lambda s_out, y_out, ws: fn(rp, ids, w, k, SEED, flags=flags, s_out=s_out, y_out=y_out, ws=ws)
 
+    # autotuned stream shapes and first-pass quantile per (k, row-length bucket), untimed;
+    # --tuning-file reuses a saved table (so that a profiled run times the same tuning)
+    tuned = {}
+    ks = (args.k,) if args.only == "fastgm" else (K_MAIN, K_ALT)
+    if args.tuning_file and os.path.exists(args.tuning_file):
+        gm.tuning_load(args.tuning_file)
+        tuned = {str(k): gm.tuning_get(k, nnz // n_rows) for k in ks}
+    elif not args.no_tune:
+        for k in ks:
+            tuned[str(k)] = gm.gm_tune(rp, ids, w, k, SEED)[0]
+        if args.tuning_file:
+            gm.tuning_save(args.tuning_file)
+
     if args.only == "fastgm":
         ms, kms, st, _, _ = timed(sketch_call(gm.gm_sketch, args.k, args.flags), args.k, args.steps, args.warmup)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": world * n_rows / (ms * 1e-3), "unit": "sketches/s",
                               "ms_per_step": ms, "kernel_ms": kms, "only": "fastgm k=%d flags=%d" % (args.k, args.flags),
-                              "stats": st}),
+                              "tuning": tuned or "defaults", "stats": st}),
                   flush=True)
         return
     clocks = ClockSampler(local)
@@ -436,9 +453,11 @@ def main():
         "hbm": hbm_figures(nnz, n_rows, K_MAIN, kms_main),
         "e2e": {"value": world * n_rows / e2e_s, "unit": "sketches/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "tuning": tuned or "defaults",
         "gpu_launches": LAUNCHES_PER_CALL * args.steps,
         "clocks": clk,
     }
+    line["graph"] = graph_leg(args, timed, sketch_call, ms_main, (rp, ids, w))
     if not args.no_learned:
         line["learned_k1024"] = learned_ablation(args, timed, sketch_call, (rp, ids, w), s_main, y_main, ms_main,
                                                  st_main, n_rows)
@@ -450,6 +469,56 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def graph_leg(args, timed, sketch_call, ms_main, dev_csr):
+    """gm_sketch replayed from a CUDA graph (gm_graph_*) against direct calls: on the
+    benchmark batch, and on a small batch (64 rows, n+ ~ LogNormal(ln 300, 1),
+    k = 256) where the host-side cost of five launches is visible."""
+    import torch
+    from paper_2302_05176_gb300 import gm
+    from paper_2302_05176_gb300 import workloads as W
+
+    def time_replays(g, steps):
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def time_direct(csr, k, steps):
+        rp, ids, w = csr
+        s = torch.empty((rp.numel() - 1, k), dtype=torch.int32, device="cuda")
+        y = torch.empty((rp.numel() - 1, k), dtype=torch.float64, device="cuda")
+        ws = gm.workspace(rp.numel() - 1, ids.numel(), k)
+        for _ in range(3):
+            gm.gm_sketch(rp, ids, w, k, SEED, s_out=s, y_out=y, ws=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            gm.gm_sketch(rp, ids, w, k, SEED, s_out=s, y_out=y, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    rp, ids, w = dev_csr
+    g = gm.SketchGraph(rp, ids, w, K_MAIN, SEED)
+    big = time_replays(g, args.steps)
+    g.close()
+    small = gm.to_device(W.lognormal_batch(seed=SEED + 100, n_rows=64, median=300.0))
+    g2 = gm.SketchGraph(*small, 256, SEED)
+    small_graph = time_replays(g2, 200)
+    g2.close()
+    small_direct = time_direct(small, 256, 200)
+    return {"ms_per_step_graph": big, "ms_per_step_direct": ms_main,
+            "small_batch": {"rows": 64, "k": 256, "nnz": int(small[1].numel()),
+                            "ms_per_call_graph": small_graph, "ms_per_call_direct": small_direct}}
 
 
 SERVE_RATE = 20_000.0

@@ -62,15 +62,15 @@ extern "C" {
  * == nnz, ids >= 0, weights finite and >= 0.  A violation sets GM_EDATA in the
  * device status (gm_status); the registers of an invalid row are unspecified. */
 #define GM_FLAG_VALIDATE (1u << 0)
-/* Compute -ln(u), the products and 1/v on the FP64 unit (CUDA's log, IEEE
- * multiply and reciprocal) instead of the default exact integer-pipe arithmetic.
- * Products and reciprocals are bit-identical either way; the two logarithms
- * differ by at most one ulp.  Slower on GB300; kept for comparison. */
+/* Arithmetic of an arrival.  Default: -ln(u) exactly on the integer pipes (a
+ * table-driven logarithm in 128-bit fixed point), the two products of each
+ * arrival and 1/v on the FP64 unit (IEEE multiply and reciprocal), which is
+ * otherwise idle.  GM_FLAG_INT_PRODUCTS computes the products and 1/v on the
+ * integer pipes too (the same bits; slower on GB300).  GM_FLAG_FP64_UNIT also
+ * takes -ln(u) from the FP64 unit (CUDA's log: within one ulp of the default;
+ * much slower on GB300).  All three are kept for comparison and tested. */
+#define GM_FLAG_INT_PRODUCTS (1u << 1)
 #define GM_FLAG_FP64_UNIT (1u << 2)
-/* Compute -ln(u) on the integer pipes but the two products of each arrival and
- * 1/v on the FP64 unit (IEEE multiply and reciprocal: the same bits).  Same
- * registers as the default; a throughput choice.  Ignored with GM_FLAG_FP64_UNIT. */
-#define GM_FLAG_FP64_PRODUCTS (1u << 1)
 /* Testing aid: divide the closed-form bounds of the first pass (and of long-row
  * chunks) by 8, so that most rows find a register unfilled and take the
  * escalation paths.  The registers are the same; only the work grows. */
@@ -274,6 +274,53 @@ size_t gm_sketch_learned_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k)
 int gm_sketch_learned(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
                       int32_t k, uint64_t seed, uint32_t flags, const float* params, float margin, int32_t* s_out,
                       double* y_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- autotuning ---------------------------------------------------------------
+ * Not in the paper.  Four runtime parameters shape gm_sketch's work without
+ * changing its output: the quantile of the first-pass bound (p_first: the bound
+ * is the (1 - p_first) quantile of y* given sum v) and the routing of elements by
+ * their expected number of arrivals below the bound -- one lane each up to
+ * light_max, 8-lane segments up to medium_max, 32-lane warps up to heavy_max,
+ * a dense permutation beyond.  gm_sketch takes them from a process-wide table
+ * keyed by (k, floor(log2(mean row length))), else the defaults (0.05, 6, 48,
+ * 256).  gm_tune times candidate values on the caller's batch (coordinate
+ * descent, each candidate the faster of two timed calls after one warm-up; it
+ * synchronises `stream`), installs the fastest for that key and returns it.
+ * Requires 0 < p_first < 1 and 0 < light_max <= medium_max <= heavy_max. */
+typedef struct gm_tuning {
+  float p_first;
+  float light_max;
+  float medium_max;
+  float heavy_max;
+} gm_tuning;
+void gm_tuning_default(gm_tuning* t);
+int gm_tune(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz, int32_t k,
+            uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace, size_t workspace_bytes,
+            gm_tuning* best, double* best_ms, void* stream);
+/* Install / read / forget table entries (mean_row_len = nnz / n_rows of the
+ * batches the entry serves); save and load the table as text. */
+int gm_tuning_set(int32_t k, int64_t mean_row_len, const gm_tuning* t);
+int gm_tuning_get(int32_t k, int64_t mean_row_len, gm_tuning* out);
+int gm_tuning_clear(void);
+int gm_tuning_save(const char* path);
+int gm_tuning_load(const char* path);
+
+/* ---- CUDA graphs --------------------------------------------------------------
+ * Not in the paper.  A gm_sketch call is five kernel launches plus host-side
+ * setup; for a workload repeated over the same buffers (a fixed-shape batch
+ * refilled in place, a benchmark loop) the whole call can be captured once into
+ * a CUDA graph and replayed with one launch.  gm_graph_create captures
+ * gm_sketch(row_ptr, ..., workspace_bytes) on a private stream (nothing runs);
+ * gm_graph_launch replays it on `stream`, reading whatever the buffers hold at
+ * that time (the sizes, k, seed and flags are fixed; row_ptr's values may change
+ * as long as they stay a valid CSR of nnz elements).  Errors as gm_sketch;
+ * GM_ECUDA if capture or instantiation fails. */
+typedef struct gm_graph gm_graph;
+int gm_graph_create(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
+                    int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
+                    size_t workspace_bytes, gm_graph** out);
+int gm_graph_launch(gm_graph* graph, void* stream);
+int gm_graph_destroy(gm_graph* graph);
 
 /* Human-readable text of a status code (static storage, never NULL). */
 const char* gm_strerror(int code);

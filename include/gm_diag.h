@@ -51,7 +51,9 @@ int gm_diag_first_arrival(const int32_t* ids, const double* v, int64_t n, int32_
  * computed independently per element (for instruction counting): out[i] = the
  * arrival time of step z = i mod k of element ids[i] with R = R[i] (a
  * single-term sum), jout[i] its RandInt target, screened[i] the screen decision
- * for weight R[i] and bound T.  ctab_scratch: >= k doubles.  1 <= k <= GM_MAX_K. */
+ * for weight R[i] and bound T.  Three kernels: the arrival in the default
+ * arithmetic, the arrival with GM_FLAG_INT_PRODUCTS' arithmetic (same outputs,
+ * written last), the screen.  ctab_scratch: >= k doubles.  1 <= k <= GM_MAX_K. */
 int gm_diag_arrival_cost(const int32_t* ids, const double* R, int64_t n, int32_t k, uint64_t seed,
                          double* ctab_scratch, double* out, int32_t* jout, uint8_t* screened, float T,
                          void* stream);

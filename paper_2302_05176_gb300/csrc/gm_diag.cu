@@ -88,6 +88,7 @@ __global__ void diag_fma_kernel(T* out, int iters, T a, T b) {
 // One arrival's value chain per thread, each independent: Philox, -ln u, the
 // product by C_z, the exact sum (a single term), its rounding, the product by R
 // and RandInt -- the algorithmic work of one arrival, for instruction counting.
+template <int ARITH>
 __global__ void diag_arrival_cost_kernel(const int32_t* __restrict__ ids, const double* __restrict__ R, int64_t n,
                                          int k, uint32_t key0, uint32_t key1, const double* __restrict__ ctab,
                                          double* __restrict__ out, int32_t* __restrict__ jout) {
@@ -95,8 +96,8 @@ __global__ void diag_arrival_cost_kernel(const int32_t* __restrict__ ids, const 
     const int z = (int)(i % k);
     const Words wd = philox((uint32_t)ids[i], (uint32_t)z, key0, key1);
     Fix acc = fix_zero();
-    fix_add(acc, fix_from(dmul_normal(neglog_u(wd.w0, wd.w1), __ldg(ctab + z))));
-    out[i] = dmul_pos(fix_round(acc), R[i]);
+    fix_add(acc, fix_from(arr_mul_t<ARITH>(arr_neglog<ARITH>(wd), __ldg(ctab + z))));
+    out[i] = arr_mul<ARITH>(fix_round(acc), R[i]);
     jout[i] = randint(wd.w2, wd.w3, z, k);
   }
 }
@@ -211,7 +212,10 @@ extern "C" int gm_diag_arrival_cost(const int32_t* ids, const double* R, int64_t
   cudaStream_t st = (cudaStream_t)stream;
   const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
   gm::diag_ctab_kernel<<<(k + 255) / 256, 256, 0, st>>>(ctab_scratch, k);
-  gm::diag_arrival_cost_kernel<<<gm::grid_for(n), 256, 0, st>>>(ids, R, n, k, k0, k1, ctab_scratch, out, jout);
+  gm::diag_arrival_cost_kernel<gm::ARITH_MIX><<<gm::grid_for(n), 256, 0, st>>>(ids, R, n, k, k0, k1, ctab_scratch,
+                                                                               out, jout);
+  gm::diag_arrival_cost_kernel<gm::ARITH_INT><<<gm::grid_for(n), 256, 0, st>>>(ids, R, n, k, k0, k1, ctab_scratch,
+                                                                               out, jout);
   gm::diag_screen_cost_kernel<<<gm::grid_for(n), 256, 0, st>>>(ids, R, n, k, k0, k1, T, screened);
   return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
 }

@@ -33,6 +33,10 @@
 
 #include <cmath>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "gm.h"
 #include "gm_device.cuh"
@@ -44,9 +48,13 @@ namespace gm {
 constexpr int BLOCK = 512;
 constexpr int WARPS = BLOCK / 32;
 constexpr int MAPCAP = 16;              // displaced positions a light lane can track
-constexpr float LIGHT_MAX = 6.0f;       // expected arrivals <= T: light lane path up to this,
-constexpr float MEDIUM_MAX = 48.0f;     //   8-lane segments up to this,
-constexpr float HEAVY_MAX = 256.0f;     //   32-lane warps up to this, dense permutation beyond
+// Default routing by the expected number of arrivals below T (gm_tuning): light
+// lanes up to LIGHT_MAX, 8-lane segments up to MEDIUM_MAX, 32-lane warps up to
+// HEAVY_MAX, dense permutations beyond; first-pass bound at quantile 1 - P_FIRST.
+constexpr float LIGHT_MAX = 6.0f;
+constexpr float MEDIUM_MAX = 48.0f;
+constexpr float HEAVY_MAX = 256.0f;
+constexpr float P_FIRST = 0.05f;
 constexpr int MED_SW = 8;
 constexpr int MED_SLOTS = 128;          // hash slots per 8-lane segment
 constexpr int MED_MAX_FILL = 96;        // beyond: the element moves to a 32-lane warp
@@ -84,6 +92,7 @@ struct SketchArgs {
   int ndense;             // dense permutations per CTA (warps that take super-heavy elements)
   float q1, q2, q_split;  // normalised bounds: first pass, later passes, long rows (inf = none)
   const float* t_row;     // learned first-pass bound per row (absolute), or null
+  float light_max, medium_max, heavy_max;  // routing thresholds (expected arrivals below T)
 };
 
 struct SmemScalars {
@@ -94,6 +103,7 @@ struct SmemScalars {
   unsigned long long clk[WARPS][NCLK];  // light, 8-lane, 32-lane, dense, barrier wait, setup, finish, total
 };
 __shared__ SmemScalars sh_scalars;
+
 
 // Shared memory of the FastGM kernel: registers | light maps, 8-lane hashes or
 // warp hashes | ndense dense permutations | per-warp screening buffers.
@@ -197,7 +207,7 @@ __device__ __forceinline__ void seg_phase(const SketchArgs& a, int64_t lo, uint6
 // --------------------------------------------------------------------------
 // Light path with warp screening.  Elements [lo, lo+n) of the unit; T as bits and
 // as an FP32 value (equal as reals).  Elements expected to need more than
-// LIGHT_MAX arrivals go to the work list, tagged by their expected count.
+// a.light_max arrivals go to the work list, tagged by their expected count.
 // --------------------------------------------------------------------------
 template <int ARITH>
 __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int n, uint64_t Tbits, float Tf,
@@ -232,8 +242,8 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
             ++cnt.elements;
             const float vf = f32_trunc(v);
             const float lam = kf * (1.0f - __expf(-(vf * Tf)));  // expected arrivals <= T (routing only)
-            if (lam > LIGHT_MAX) {
-              const uint32_t tag = lam > HEAVY_MAX ? TAG_SUPER : (lam > MEDIUM_MAX ? TAG_HEAVY : TAG_MEDIUM);
+            if (lam > a.light_max) {
+              const uint32_t tag = lam > a.heavy_max ? TAG_SUPER : (lam > a.medium_max ? TAG_HEAVY : TAG_MEDIUM);
               a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | tag;
             } else {
               const Words wd = philox((uint32_t)a.ids[lo + slot], 0u, a.key0, a.key1);
@@ -961,9 +971,45 @@ static int launch_all(const SketchArgs& a, bool plain, int nsm, cudaStream_t str
   return GM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Tuning table: (k, floor(log2(mean row length))) -> gm_tuning.
+// ---------------------------------------------------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, gm_tuning> g_tune;
+
+static int tune_bucket(int64_t mean_len) {
+  int b = 0;
+  while (b < 62 && ((int64_t)1 << (b + 1)) <= mean_len) ++b;
+  return b;
+}
+static bool tuning_ok(const gm_tuning& t) {
+  return t.p_first > 0.0f && t.p_first < 1.0f && t.light_max > 0.0f && t.light_max <= t.medium_max &&
+         t.medium_max <= t.heavy_max && std::isfinite(t.heavy_max);
+}
+static gm_tuning tuning_for(int k, int32_t n_rows, int64_t nnz) {
+  gm_tuning t{P_FIRST, LIGHT_MAX, MEDIUM_MAX, HEAVY_MAX};
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tune.find({k, tune_bucket(n_rows > 0 ? nnz / n_rows : 0)});
+  if (it != g_tune.end()) t = it->second;
+  return t;
+}
+
+static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
+                               int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out,
+                               void* workspace, size_t workspace_bytes, cudaStream_t stream, bool plain,
+                               const float* t_row, const gm_tuning* tuning);
+
 int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
                   int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
                   size_t workspace_bytes, cudaStream_t stream, bool plain, const float* t_row) {
+  return launch_sketch_tuned(row_ptr, ids, w, n_rows, nnz, k, seed, flags, s_out, y_out, workspace, workspace_bytes,
+                             stream, plain, t_row, nullptr);
+}
+
+static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
+                               int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out,
+                               void* workspace, size_t workspace_bytes, cudaStream_t stream, bool plain,
+                               const float* t_row, const gm_tuning* tuning) {
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K) return GM_EINVAL;
   if (nnz > 0x7FFFFFFFll) return GM_EINVAL;
   if (!workspace || !row_ptr || (n_rows > 0 && (!s_out || !y_out)) || (nnz > 0 && (!ids || !w)))
@@ -1001,10 +1047,15 @@ int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, i
   a.esc = L.esc;
   a.max_long = (int)L.max_long;
   a.t_row = plain ? nullptr : t_row;
+  const gm_tuning tn = tuning ? *tuning : tuning_for(k, n_rows, nnz);
+  if (!tuning_ok(tn)) return GM_EINVAL;
+  a.light_max = tn.light_max;
+  a.medium_max = tn.medium_max;
+  a.heavy_max = tn.heavy_max;
   if (bound == GM_BOUND_NONE) {
     a.q1 = a.q2 = a.q_split = INFINITY;
   } else {
-    a.q1 = (float)quantile_bound(0.05, k);
+    a.q1 = (float)quantile_bound((double)tn.p_first, k);
     a.q2 = (float)quantile_bound(1e-6, k);
     a.q_split = (float)quantile_bound(1e-3, k);
     if (flags & GM_FLAG_TIGHT_BOUND) {
@@ -1018,9 +1069,9 @@ int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, i
   if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
     return GM_ECUDA;
   a.ndense = dense_buffers(k, (size_t)smem_sm);
-  const int rc = (flags & GM_FLAG_FP64_UNIT)       ? launch_all<ARITH_FP64>(a, plain, nsm, stream)
-                 : (flags & GM_FLAG_FP64_PRODUCTS) ? launch_all<ARITH_MIX>(a, plain, nsm, stream)
-                                                   : launch_all<ARITH_INT>(a, plain, nsm, stream);
+  const int rc = (flags & GM_FLAG_FP64_UNIT)      ? launch_all<ARITH_FP64>(a, plain, nsm, stream)
+                 : (flags & GM_FLAG_INT_PRODUCTS) ? launch_all<ARITH_INT>(a, plain, nsm, stream)
+                                                  : launch_all<ARITH_MIX>(a, plain, nsm, stream);
   if (rc != GM_OK) return rc;
   return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
 }
@@ -1050,8 +1101,141 @@ extern "C" int gm_sketch(const int64_t* row_ptr, const int32_t* ids, const doubl
 extern "C" int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
                                int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out,
                                double* y_out, void* workspace, size_t workspace_bytes, void* stream) {
-  return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags & (GM_FLAG_VALIDATE | GM_FLAG_FP64_UNIT | GM_FLAG_FP64_PRODUCTS),
+  return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags & (GM_FLAG_VALIDATE | GM_FLAG_FP64_UNIT | GM_FLAG_INT_PRODUCTS),
                            s_out, y_out, workspace, workspace_bytes, (cudaStream_t)stream, true, nullptr);
+}
+
+extern "C" void gm_tuning_default(gm_tuning* t) {
+  if (t) *t = gm_tuning{gm::P_FIRST, gm::LIGHT_MAX, gm::MEDIUM_MAX, gm::HEAVY_MAX};
+}
+
+extern "C" int gm_tuning_set(int32_t k, int64_t mean_row_len, const gm_tuning* t) {
+  if (!t || k < 1 || k > GM_MAX_K || mean_row_len < 0 || !gm::tuning_ok(*t)) return GM_EINVAL;
+  std::lock_guard<std::mutex> g(gm::g_tune_mu);
+  gm::g_tune[{k, gm::tune_bucket(mean_row_len)}] = *t;
+  return GM_OK;
+}
+
+extern "C" int gm_tuning_get(int32_t k, int64_t mean_row_len, gm_tuning* out) {
+  if (!out || k < 1 || k > GM_MAX_K || mean_row_len < 0) return GM_EINVAL;
+  gm_tuning_default(out);
+  std::lock_guard<std::mutex> g(gm::g_tune_mu);
+  auto it = gm::g_tune.find({k, gm::tune_bucket(mean_row_len)});
+  if (it == gm::g_tune.end()) return GM_EINVAL;
+  *out = it->second;
+  return GM_OK;
+}
+
+extern "C" int gm_tuning_clear(void) {
+  std::lock_guard<std::mutex> g(gm::g_tune_mu);
+  gm::g_tune.clear();
+  return GM_OK;
+}
+
+// Text: one line per entry, "k bucket p_first light_max medium_max heavy_max".
+extern "C" int gm_tuning_save(const char* path) {
+  if (!path) return GM_EINVAL;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return GM_EINVAL;
+  bool ok = std::fprintf(f, "# gm_tuning v1: k log2(mean row length) p_first light_max medium_max heavy_max\n") > 0;
+  {
+    std::lock_guard<std::mutex> g(gm::g_tune_mu);
+    for (const auto& kv : gm::g_tune)
+      ok = ok && std::fprintf(f, "%d %d %.9g %.9g %.9g %.9g\n", kv.first.first, kv.first.second, kv.second.p_first,
+                              kv.second.light_max, kv.second.medium_max, kv.second.heavy_max) > 0;
+  }
+  return (std::fclose(f) == 0 && ok) ? GM_OK : GM_EINVAL;
+}
+
+extern "C" int gm_tuning_load(const char* path) {
+  if (!path) return GM_EINVAL;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return GM_EINVAL;
+  char line[256];
+  std::vector<std::pair<std::pair<int, int>, gm_tuning>> got;
+  bool ok = true;
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    int k = 0, b = 0;
+    gm_tuning t{};
+    if (std::sscanf(line, "%d %d %f %f %f %f", &k, &b, &t.p_first, &t.light_max, &t.medium_max, &t.heavy_max) != 6 ||
+        k < 1 || k > GM_MAX_K || b < 0 || b > 62 || !gm::tuning_ok(t)) {
+      ok = false;
+      break;
+    }
+    got.push_back({{k, b}, t});
+  }
+  std::fclose(f);
+  if (!ok) return GM_EDATA;
+  std::lock_guard<std::mutex> g(gm::g_tune_mu);
+  for (const auto& e : got) gm::g_tune[e.first] = e.second;
+  return GM_OK;
+}
+
+extern "C" int gm_tune(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
+                       int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
+                       size_t workspace_bytes, gm_tuning* best, double* best_ms, void* stream) {
+  if (!best || k < 1 || k > GM_MAX_K || n_rows < 0 || nnz < 0) return GM_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return GM_ECUDA;
+  }
+  auto run = [&](const gm_tuning& t, float* ms) -> int {
+    int rc = gm::launch_sketch_tuned(row_ptr, ids, w, n_rows, nnz, k, seed, flags, s_out, y_out, workspace,
+                                     workspace_bytes, st, false, nullptr, &t);
+    if (rc != GM_OK) return rc;
+    float fastest = INFINITY;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (cudaEventRecord(e0, st) != cudaSuccess) return GM_ECUDA;
+      rc = gm::launch_sketch_tuned(row_ptr, ids, w, n_rows, nnz, k, seed, flags, s_out, y_out, workspace,
+                                   workspace_bytes, st, false, nullptr, &t);
+      if (rc != GM_OK) return rc;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return GM_ECUDA;
+      float m = 0.0f;
+      if (cudaEventElapsedTime(&m, e0, e1) != cudaSuccess) return GM_ECUDA;
+      fastest = m < fastest ? m : fastest;
+    }
+    *ms = fastest;
+    return GM_OK;
+  };
+  gm_tuning cur = gm::tuning_for(k, n_rows, nnz);
+  float t_cur = 0.0f;
+  int rc = run(cur, &t_cur);
+  const float p_cand[] = {0.01f, 0.02f, 0.05f, 0.1f, 0.2f, 0.35f};
+  const float l_cand[] = {3.0f, 4.0f, 6.0f, 8.0f, 11.0f};
+  const float m_cand[] = {24.0f, 32.0f, 48.0f, 64.0f, 96.0f};
+  const float h_cand[] = {128.0f, 256.0f, 512.0f, 1024.0f};
+  struct Axis {
+    float gm_tuning::*field;
+    const float* vals;
+    int n;
+  } axes[] = {{&gm_tuning::p_first, p_cand, 6}, {&gm_tuning::light_max, l_cand, 5},
+              {&gm_tuning::medium_max, m_cand, 5}, {&gm_tuning::heavy_max, h_cand, 4}};
+  for (const Axis& ax : axes) {
+    for (int i = 0; i < ax.n && rc == GM_OK; ++i) {
+      gm_tuning t = cur;
+      t.*(ax.field) = ax.vals[i];
+      if (t.*(ax.field) == cur.*(ax.field) || !gm::tuning_ok(t)) continue;
+      float ms = 0.0f;
+      rc = run(t, &ms);
+      if (rc == GM_OK && ms < 0.98f * t_cur) {
+        cur = t;
+        t_cur = ms;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != GM_OK) return rc;
+  {
+    std::lock_guard<std::mutex> g(gm::g_tune_mu);
+    gm::g_tune[{k, gm::tune_bucket(n_rows > 0 ? nnz / n_rows : 0)}] = cur;
+  }
+  *best = cur;
+  if (best_ms) *best_ms = t_cur;
+  return GM_OK;
 }
 
 // ---------------------------------------------------------------------------

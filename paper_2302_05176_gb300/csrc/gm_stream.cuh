@@ -9,12 +9,12 @@
 
 namespace gm {
 
-// Arithmetic of an arrival: ARITH_INT computes -ln u, the products and 1/v on the
-// integer pipes (gm_arith.cuh); ARITH_FP64 uses the FP64 unit (CUDA's log and the
-// IEEE product / reciprocal), kept for comparison; ARITH_MIX takes -ln u from the
-// integer pipes and the products and 1/v from the FP64 unit, which is otherwise
-// idle.  Products and reciprocals are bit-identical in all three; the logarithms
-// of ARITH_FP64 differ from the other two by at most an ulp.
+// Arithmetic of an arrival.  ARITH_MIX (the default) takes -ln u from the integer
+// pipes (gm_arith.cuh) and the products and 1/v from the FP64 unit, which is
+// otherwise idle; ARITH_INT computes the products and 1/v on the integer pipes
+// too; ARITH_FP64 uses the FP64 unit throughout (CUDA's log).  Products and
+// reciprocals are bit-identical in all three; the logarithms of ARITH_FP64
+// differ from the other two by at most an ulp.
 constexpr int ARITH_FP64 = 0;
 constexpr int ARITH_INT = 1;
 constexpr int ARITH_MIX = 2;

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libgm.so")
 GM_OK, GM_EINVAL, GM_ENOMEM, GM_ECUDA, GM_ETIMEOUT, GM_EDATA = 0, 1, 2, 3, 4, 5
 GM_FLAG_VALIDATE = 1 << 0
 GM_FLAG_FP64_UNIT = 1 << 2
-GM_FLAG_FP64_PRODUCTS = 1 << 1
+GM_FLAG_INT_PRODUCTS = 1 << 1
 GM_FLAG_TIGHT_BOUND = 1 << 3
 GM_BOUND_CLOSED = 0 << 4
 GM_BOUND_NONE = 1 << 4
@@ -46,6 +46,14 @@ class gm_stats(ctypes.Structure):
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+
+
+class gm_tuning(ctypes.Structure):
+    _fields_ = [("p_first", ctypes.c_float), ("light_max", ctypes.c_float), ("medium_max", ctypes.c_float),
+                ("heavy_max", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: float(getattr(self, f)) for f, _ in self._fields_}
 
 
 _lib = None
@@ -83,6 +91,19 @@ def lib():
         L.gm_sketch_learned_workspace_bytes.restype = ctypes.c_size_t
         L.gm_sketch_learned.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                         ctypes.c_uint32, _vp, ctypes.c_float, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+        L.gm_graph_create.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                      ctypes.c_uint32, _vp, _vp, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]
+        L.gm_graph_launch.argtypes = [_vp, _vp]
+        L.gm_graph_destroy.argtypes = [_vp]
+        tp = ctypes.POINTER(gm_tuning)
+        L.gm_tuning_default.argtypes = [tp]
+        L.gm_tuning_default.restype = None
+        L.gm_tune.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                              ctypes.c_uint32, _vp, _vp, _vp, ctypes.c_size_t, tp, ctypes.POINTER(ctypes.c_double), _vp]
+        L.gm_tuning_set.argtypes = [ctypes.c_int32, ctypes.c_int64, tp]
+        L.gm_tuning_get.argtypes = [ctypes.c_int32, ctypes.c_int64, tp]
+        L.gm_tuning_save.argtypes = [ctypes.c_char_p]
+        L.gm_tuning_load.argtypes = [ctypes.c_char_p]
         L.gm_strerror.argtypes = [ctypes.c_int]
         L.gm_strerror.restype = ctypes.c_char_p
         L.gm_version.restype = ctypes.c_char_p
@@ -317,3 +338,92 @@ def gm_sketch_learned(row_ptr, ids, w, k, seed, params, margin=0.0, flags=0, s_o
                                  _ptr(s_out), _ptr(y_out), _ptr(ws), ws.numel(), _stream_handle(stream))
     _check(rc, "gm_sketch_learned")
     return s_out, y_out, ws
+
+
+class SketchGraph:
+    """One gm_sketch call over fixed buffers, captured as a CUDA graph (gm_graph_*).
+    replay() re-runs it on whatever the buffers hold; s / y are the outputs."""
+
+    def __init__(self, row_ptr, ids, w, k, seed, flags=0, s_out=None, y_out=None, ws=None):
+        _need_cuda(row_ptr, torch.int64, "row_ptr")
+        _need_cuda(ids, torch.int32, "ids")
+        _need_cuda(w, torch.float64, "w")
+        n_rows, nnz = row_ptr.numel() - 1, ids.numel()
+        dev = row_ptr.device
+        self.s = torch.empty((n_rows, k), dtype=torch.int32, device=dev) if s_out is None else s_out
+        self.y = torch.empty((n_rows, k), dtype=torch.float64, device=dev) if y_out is None else y_out
+        self.ws = workspace(n_rows, nnz, k, flags, dev) if ws is None else ws
+        self._keep = (row_ptr, ids, w)
+        h = _vp()
+        _check(lib().gm_graph_create(_ptr(row_ptr), _ptr(ids), _ptr(w), n_rows, nnz, int(k),
+                                     int(seed) & 0xFFFFFFFFFFFFFFFF, int(flags), _ptr(self.s), _ptr(self.y),
+                                     _ptr(self.ws), self.ws.numel(), ctypes.byref(h)), "gm_graph_create")
+        self._h = h
+
+    def replay(self, stream=None):
+        _check(lib().gm_graph_launch(self._h, _stream_handle(stream)), "gm_graph_launch")
+        return self.s, self.y
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gm_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- autotuning (gm_tune / gm_tuning_*) -------------------------------------------------------
+
+def tuning_default():
+    t = gm_tuning()
+    lib().gm_tuning_default(ctypes.byref(t))
+    return t.as_dict()
+
+
+def _tuning(d):
+    t = gm_tuning()
+    lib().gm_tuning_default(ctypes.byref(t))
+    for f, v in d.items():
+        setattr(t, f, float(v))
+    return t
+
+
+def gm_tune(row_ptr, ids, w, k, seed, flags=0, s_out=None, y_out=None, ws=None, stream=None):
+    """Time candidate tunings on this batch; installs and returns (best dict, best ms)."""
+    n_rows, nnz = row_ptr.numel() - 1, ids.numel()
+    dev = row_ptr.device
+    s_out = torch.empty((n_rows, k), dtype=torch.int32, device=dev) if s_out is None else s_out
+    y_out = torch.empty((n_rows, k), dtype=torch.float64, device=dev) if y_out is None else y_out
+    ws = workspace(n_rows, nnz, k, flags, dev) if ws is None else ws
+    best = gm_tuning()
+    ms = ctypes.c_double()
+    _check(lib().gm_tune(_ptr(row_ptr), _ptr(ids), _ptr(w), n_rows, nnz, int(k), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                         int(flags), _ptr(s_out), _ptr(y_out), _ptr(ws), ws.numel(), ctypes.byref(best),
+                         ctypes.byref(ms), _stream_handle(stream)), "gm_tune")
+    return best.as_dict(), ms.value
+
+
+def tuning_set(k, mean_row_len, **values):
+    _check(lib().gm_tuning_set(int(k), int(mean_row_len), ctypes.byref(_tuning(values))), "gm_tuning_set")
+
+
+def tuning_get(k, mean_row_len):
+    """The table entry for (k, mean row length), or None."""
+    t = gm_tuning()
+    return t.as_dict() if lib().gm_tuning_get(int(k), int(mean_row_len), ctypes.byref(t)) == GM_OK else None
+
+
+def tuning_clear():
+    lib().gm_tuning_clear()
+
+
+def tuning_save(path):
+    _check(lib().gm_tuning_save(os.fsencode(path)), "gm_tuning_save")
+
+
+def tuning_load(path):
+    _check(lib().gm_tuning_load(os.fsencode(path)), "gm_tuning_load")

@@ -25,14 +25,14 @@ def run(fn, X, k, seed, flags=gm.GM_FLAG_VALIDATE):
     return s.cpu().numpy(), y.cpu().numpy(), stats
 
 
-def check(X, k, seed, flags=gm.GM_FLAG_VALIDATE, variants=("fastgm", "plain", "fastgm_fp64", "fastgm_mix")):
+def check(X, k, seed, flags=gm.GM_FLAG_VALIDATE, variants=("fastgm", "plain", "fastgm_fp64", "fastgm_int")):
     """Every variant against the oracle; FastGM and plain bit-identical within one arithmetic,
-    and the integer-pipe and mixed arithmetics bit-identical to each other."""
+    and the default (mixed) and all-integer arithmetics bit-identical to each other."""
     s_ref, y_ref, y2_ref = oracle.sketch(X.row_ptr, X.ids, X.w, k, seed, want_y2=True)
     table = {"fastgm": (gm.gm_sketch, 0), "plain": (gm.gm_sketch_plain, 0),
              "fastgm_fp64": (gm.gm_sketch, gm.GM_FLAG_FP64_UNIT), "plain_fp64": (gm.gm_sketch_plain, gm.GM_FLAG_FP64_UNIT),
-             "fastgm_mix": (gm.gm_sketch, gm.GM_FLAG_FP64_PRODUCTS),
-             "plain_mix": (gm.gm_sketch_plain, gm.GM_FLAG_FP64_PRODUCTS)}
+             "fastgm_int": (gm.gm_sketch, gm.GM_FLAG_INT_PRODUCTS),
+             "plain_int": (gm.gm_sketch_plain, gm.GM_FLAG_INT_PRODUCTS)}
     outs = {}
     for name in variants:
         fn, extra = table[name]
@@ -41,7 +41,7 @@ def check(X, k, seed, flags=gm.GM_FLAG_VALIDATE, variants=("fastgm", "plain", "f
         rep = compare_sketch(s, y, s_ref, y_ref, y2_ref)
         assert rep["ok"], (name, rep)
         outs[name] = (s, y, stats, rep)
-    for a, b in (("fastgm", "plain"), ("fastgm_fp64", "plain_fp64"), ("fastgm", "fastgm_mix"), ("plain", "plain_mix")):
+    for a, b in (("fastgm", "plain"), ("fastgm_fp64", "plain_fp64"), ("fastgm", "fastgm_int"), ("plain", "plain_int")):
         if a in outs and b in outs:
             assert np.array_equal(outs[a][0], outs[b][0])
             assert np.array_equal(outs[a][1].view(np.int64), outs[b][1].view(np.int64))
@@ -50,7 +50,7 @@ def check(X, k, seed, flags=gm.GM_FLAG_VALIDATE, variants=("fastgm", "plain", "f
 
 def test_single_vector_k128():
     X = W.single_vector(seed=1)
-    outs = check(X, 128, 1, variants=("fastgm", "plain", "fastgm_fp64", "plain_fp64", "fastgm_mix", "plain_mix"))
+    outs = check(X, 128, 1, variants=("fastgm", "plain", "fastgm_fp64", "plain_fp64", "fastgm_int", "plain_int"))
     assert outs["fastgm"][2]["arrivals"] < 0.2 * outs["plain"][2]["arrivals"]  # FastGM prunes
 
 
