@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--tuning-file", default=None, help="load the tuning table from this file if it exists, "
                     "else tune and save it there")
     ap.add_argument("--serve-requests", type=int, default=400, help="requests in the serving stream")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
+    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-flags", type=int, default=0)
+    ap.add_argument("--serve-stage-pinned", action="store_true")
     ap.add_argument("--learned-rows", type=int, default=200_000, help="sketches in the bound network's training set")
     ap.add_argument("--learned-steps", type=int, default=400, help="Adam steps of the bound network")
     ap.add_argument("--arith", action="store_true",
@@ -309,6 +313,14 @@ def main():
         return run_reference(args)
     if args.arith:
         return run_arith(args)
+    if args.serve_only:
+        import torch
+        from paper_2302_05176_gb300 import gm
+        gm.lib()
+        print(json.dumps({"serving": serving_leg(args), "serve_flags": args.serve_flags,
+                          "serve_stage_pinned": args.serve_stage_pinned, "serve_streams": args.serve_streams}),
+              flush=True)
+        return
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -537,7 +549,8 @@ def serving_leg(args):
     bufs = {i: (torch.from_numpy(r.csr.ids).pin_memory(), torch.from_numpy(r.csr.w).pin_memory())
             for i, r in enumerate(reqs) if r.kind == "sketch"}  # a front end receives into page-locked memory
     gen_s = time.perf_counter() - t0
-    with S.Server(seed=SEED, device_bytes=16 << 30, n_streams=2) as srv:
+    with S.Server(seed=SEED, device_bytes=16 << 30, n_streams=args.serve_streams, flags=args.serve_flags,
+                  stage_pinned=args.serve_stage_pinned) as srv:
         rng = np.random.default_rng(7)
         warm = [srv.submit_sketch(rng.choice(1 << 24, 1000, replace=False).astype(np.int32),
                                   rng.exponential(size=1000), k) for k in (256, 1024, 4096)]
@@ -584,6 +597,8 @@ def serving_leg(args):
             "query_p99_ms": pct(lat["jaccard"] + lat["cardinality"], 99),
             "sketch_batches": st["sketch_batches"], "query_batches": st["query_batches"],
             "mean_batch_rows": float(np.mean(batch)), "arena_peak_bytes": st["arena_peak_bytes"],
+            "staged_requests": st["staged_requests"], "direct_requests": st["direct_requests"],
+            "scheduler_pack_ms": st["pack_ns"] / 1e6, "scheduler_launch_ms": st["launch_ns"] / 1e6,
             "input": "pinned host buffers, copied by the engine inside the measured latency",
             "generate_s": gen_s}
 

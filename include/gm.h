@@ -305,6 +305,49 @@ int gm_tuning_clear(void);
 int gm_tuning_save(const char* path);
 int gm_tuning_load(const char* path);
 
+/* ---- FastSearch's schedule and caller-given bounds --------------------------------
+ * gm_sketch_budget: the release step of FastSearch (Algorithm 1, Sec. 2.2): in
+ * row r, element i releases the first min(k, ceil(R_row[r] * (v_i / sum v)))
+ * arrivals of its stream (sum over the row's positive weights; the ratio and the
+ * product in FP64, round to nearest, then the ceiling), and the registers keep the
+ * minima of those arrivals.  R_row: device doubles [n_rows].  Registers that no
+ * released arrival reached read (+inf, -1).  Same workspace as gm_sketch.
+ *
+ * gm_sketch_bounded: FastGM with the first-pass bound of each row given by the
+ * caller, bound_row[r] (device doubles): > 0 and finite -- that bound (rounded
+ * up to FP32); +inf -- no bound; <= 0 or NaN -- the closed form.  Any bound gives
+ * gm_sketch's registers.  With bound_row = y* of the FastSearch registers this is
+ * FastPrune.  Workspace: gm_sketch_bounded_workspace_bytes().
+ *
+ * gm_row_ystar: out[r] = max_j y[r, j] (+inf when a register is unfilled). */
+int gm_sketch_budget(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
+                     int32_t k, uint64_t seed, uint32_t flags, const double* R_row, int32_t* s_out, double* y_out,
+                     void* workspace, size_t workspace_bytes, void* stream);
+size_t gm_sketch_bounded_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k);
+int gm_sketch_bounded(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
+                      int32_t k, uint64_t seed, uint32_t flags, const double* bound_row, int32_t* s_out,
+                      double* y_out, void* workspace, size_t workspace_bytes, void* stream);
+int gm_row_ystar(const double* y, int32_t n_rows, int32_t k, double* out, void* stream);
+
+/* ---- Stream-FastGM (Algorithm 2, Sec. 3 of the paper: the extension to streams) --
+ * A stream of elements, each occurring any number of times with a fixed weight,
+ * folded chunk by chunk into one running sketch (s int32[k], y double[k] on the
+ * device, owned by the caller).  The result after any sequence of chunks is the
+ * sketch of the set of distinct elements seen: an element's arrivals depend only
+ * on (seed, id, v), so a repeated occurrence changes nothing.  Each chunk is
+ * sketched as one row whose registers start from the running sketch; once every
+ * register is filled, the chunk's bound is the running y* (FastPrune), so most
+ * elements of a long stream fail the first-arrival screen.  Duplicates inside a
+ * chunk are allowed; an id must always come with the same weight.
+ *
+ * gm_stream_reset: s = -1, y = +inf (an empty sketch).  gm_stream_ingest: fold
+ * ids/w[0..n) into (s, y); workspace of gm_stream_workspace_bytes(n, k) bytes;
+ * flags as gm_sketch except GM_BOUND_LEARNED (GM_EINVAL).  Asynchronous. */
+size_t gm_stream_workspace_bytes(int64_t n, int32_t k);
+int gm_stream_reset(int32_t* s, double* y, int32_t k, void* stream);
+int gm_stream_ingest(int32_t* s, double* y, int32_t k, const int32_t* ids, const double* w, int64_t n, uint64_t seed,
+                     uint32_t flags, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---- CUDA graphs --------------------------------------------------------------
  * Not in the paper.  A gm_sketch call is five kernel launches plus host-side
  * setup; for a workload repeated over the same buffers (a fixed-shape batch

@@ -54,7 +54,7 @@ typedef struct gm_server gm_server;
 typedef struct gm_server_config {
   size_t device_bytes;    /* device arena: batch inputs, workspaces and resident sketches */
   size_t staging_bytes;   /* pinned host staging per stream slot, for pageable inputs     */
-  int64_t max_batch_nnz;  /* elements per sketch launch                                  */
+  int64_t max_batch_nnz;  /* elements per sketch launch (a larger request runs alone)    */
   int32_t max_batch_rows; /* vectors per sketch launch                                   */
   int32_t n_streams;      /* batches in flight at once (1 .. 8)                          */
   uint64_t seed;          /* the sketch seed of every request (queries need a common seed) */
@@ -62,6 +62,8 @@ typedef struct gm_server_config {
   const float* params;    /* optional: bound network (device, GM_MODEL_PARAMS floats);
                              when set, sketches run gm_sketch_learned with margin below  */
   float margin;
+  int32_t stage_pinned;   /* 1: copy page-locked inputs through the staging area too
+                             (one DMA per batch instead of two per request)             */
   int32_t fake_device;    /* 1: no CUDA call at all; launches finish at once, sketches
                              read back empty (-1, +inf) and queries give NaN.  Tests the
                              host logic (admission, batching, cancellation) on machines
@@ -84,10 +86,15 @@ typedef struct gm_server_stats {
   uint64_t sketch_batches, query_batches, sketch_rows, sketch_elements, queries;
   uint64_t arena_bytes, arena_peak_bytes, arena_resident_bytes;
   uint64_t queued, in_flight_batches;
+  uint64_t staged_requests, direct_requests;  /* inputs copied via staging / by their own DMA */
+  uint64_t pack_ns;     /* scheduler time spent packing and launching sketch batches        */
+  uint64_t launch_ns;   /* of which inside gm_sketch / gm_sketch_learned                    */
 } gm_server_stats;
 
-/* Defaults: 8 GB arena, 64 MB staging, 2^26 elements and 4096 vectors per launch,
- * 2 streams, seed 1, closed-form bound, no model. */
+/* Defaults: 8 GB arena, 64 MB staging, 2^23 elements and 4096 vectors per launch,
+ * 4 streams, seed 1, closed-form bound, no model.  Batches of about 100 MB of
+ * input keep host-to-device copies and kernels of successive batches
+ * overlapping; much larger ones make later requests wait behind one long copy. */
 void gm_server_config_default(gm_server_config* cfg);
 
 /* Create an engine on the current CUDA device and start its scheduler thread. */

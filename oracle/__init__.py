@@ -50,7 +50,8 @@ def lib():
                                       _i32p, _f64p, _f64p]
         L.gmo_fastsearch_budgets.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int64, _i64p]
         L.gmo_fastgm_alg1.argtypes = [_i32p, _f64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
-                                      ctypes.c_int32, _i32p, _f64p, _i64p]
+                                      ctypes.c_int32, _i32p, _f64p, _i64p, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64)]
         L.gmo_stream_fastgm.argtypes = [_i32p, _f64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                         _i32p, _f64p, _i64p]
         L.gmo_jaccard.argtypes = [_i32p, _i32p, ctypes.c_int64, ctypes.c_int32, _f64p]
@@ -162,16 +163,20 @@ def fastsearch_budgets(v, R):
     return out
 
 
-def fastgm_alg1(ids, w, k, seed, delta=None):
-    """Algorithm 1 on one vector -> (s, y, arrivals generated)."""
+def fastgm_alg1(ids, w, k, seed, delta=None, search=False):
+    """Algorithm 1 on one vector -> (s, y, arrivals generated); with search=True also
+    (R at which FastSearch found every server filled, arrivals released by then)."""
     ii = np.ascontiguousarray(ids, dtype=np.int32)
     ww = np.ascontiguousarray(w, dtype=np.float64)
     s = np.zeros(k, dtype=np.int32)
     y = np.zeros(k, dtype=np.float64)
-    n_arr = ctypes.c_int64()
+    n_arr, sR, s_arr = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     rc = lib().gmo_fastgm_alg1(_p(ii, _i32p), _p(ww, _f64p), ii.size, int(k), int(seed),
-                               int(delta or k), _p(s, _i32p), _p(y, _f64p), ctypes.byref(n_arr))
+                               int(delta or k), _p(s, _i32p), _p(y, _f64p), ctypes.byref(n_arr), ctypes.byref(sR),
+                               ctypes.byref(s_arr))
     _check(rc, "fastgm_alg1")
+    if search:
+        return s, y, n_arr.value, sR.value, s_arr.value
     return s, y, n_arr.value
 
 

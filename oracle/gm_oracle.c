@@ -346,7 +346,8 @@ static double max_register(const double* y, int32_t k, int32_t* jmax) {
 }
 
 int gmo_fastgm_alg1(const int32_t* ids, const double* w, int64_t n, int32_t k, uint64_t seed,
-                    int32_t delta, int32_t* s, double* y, int64_t* arrivals_out) {
+                    int32_t delta, int32_t* s, double* y, int64_t* arrivals_out, int64_t* search_R_out,
+                    int64_t* search_arrivals_out) {
   if (k < 1 || n < 0 || delta < 1) return GMO_EINVAL;
   for (int32_t j = 0; j < k; ++j) {
     s[j] = INT32_MAX;
@@ -400,6 +401,8 @@ int gmo_fastgm_alg1(const int32_t* ids, const double* w, int64_t n, int32_t k, u
       }
     }
   }
+  if (search_R_out) *search_R_out = R;                 /* the budget at which no server was empty */
+  if (search_arrivals_out) *search_arrivals_out = arrivals;
   /* FastPrune: stream every queue until its next arrival exceeds y* (or its k arrivals are spent) */
   if (rc == GMO_OK && np > 0) {
     int32_t jstar;

@@ -36,7 +36,7 @@ struct LongRow {
   uint32_t done;       // chunks finished
   float sum;           // sum of positive weights (FP32, places the bound only)
   int npos;            // positive weights
-  uint32_t pad[2];
+  double dsum;         // FP64 sum of the positive weights (budget passes only)
 };
 
 constexpr size_t WS_HEADER_BYTES = 256;

@@ -179,6 +179,8 @@ struct Server {
   bool stop = false;
   bool paused = false;
   int in_flight = 0;
+  std::atomic<uint64_t> launch_ns_acc{0};  // written by the scheduler outside the mutex
+  std::atomic<uint64_t> pack_ns_acc{0};
   gm_server_stats st{};
 
   size_t resident_bytes() const {
@@ -361,7 +363,7 @@ static bool plan_sketch_batch(Server& S, SketchPlan& P) {
   int64_t used = 0;
   for (uint64_t t : pick) {
     const Req& r = S.reqs[t];
-    if (!S.fake && !r.pinned && used + r.nnz <= sl->staging_elems) {
+    if (!S.fake && (!r.pinned || S.cfg.stage_pinned) && used + r.nnz <= sl->staging_elems) {
       staged.push_back(t);
       used += r.nnz;
     } else {
@@ -370,6 +372,8 @@ static bool plan_sketch_batch(Server& S, SketchPlan& P) {
   }
   P.tickets = staged;
   P.tickets.insert(P.tickets.end(), direct.begin(), direct.end());
+  S.st.staged_requests += staged.size();
+  S.st.direct_requests += direct.size();
   P.staged = (int64_t)staged.size();
   P.nnz = nnz;
   P.k = k;
@@ -442,12 +446,14 @@ static int launch_sketch_batch(Server& S, SketchPlan& P, const std::vector<Req*>
       return GM_ECUDA;
   }
   int rc;
+  const int64_t t_launch = now_ns();
   if (S.cfg.params)
     rc = gm_sketch_learned(rp_d, ids_d, w_d, (int32_t)m, P.nnz, P.k, S.cfg.seed, S.cfg.flags, S.cfg.params,
                            S.cfg.margin, P.s_out, P.y_out, P.ws, P.ws_bytes, st);
   else
     rc = gm_sketch(rp_d, ids_d, w_d, (int32_t)m, P.nnz, P.k, S.cfg.seed, S.cfg.flags, P.s_out, P.y_out, P.ws,
                    P.ws_bytes, st);
+  S.launch_ns_acc += (uint64_t)(now_ns() - t_launch);
   if (rc != GM_OK) return rc;
   // the workspace header's status word (written by the sketch kernels)
   if (cudaMemcpyAsync(sl.h_status, P.ws, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return GM_ECUDA;
@@ -571,7 +577,9 @@ static void scheduler(Server* Sp) {
           int rc = GM_OK;
           if (!S.fake) {
             lk.unlock();
+            const int64_t t0 = now_ns();
             rc = launch_sketch_batch(S, P, rq);
+            S.pack_ns_acc += (uint64_t)(now_ns() - t0);
             if (rc != GM_OK) cudaStreamSynchronize(P.slot->stream);  // no copy may land after the free
             lk.lock();
           }
@@ -626,9 +634,9 @@ extern "C" void gm_server_config_default(gm_server_config* c) {
   std::memset(c, 0, sizeof(*c));
   c->device_bytes = (size_t)8 << 30;
   c->staging_bytes = (size_t)64 << 20;
-  c->max_batch_nnz = (int64_t)1 << 26;
+  c->max_batch_nnz = (int64_t)1 << 23;
   c->max_batch_rows = 4096;
-  c->n_streams = 2;
+  c->n_streams = 4;
   c->seed = 1;
   c->flags = 0;
   c->params = nullptr;
@@ -722,7 +730,8 @@ extern "C" int gm_server_submit_sketch(gm_server* h, const int32_t* ids, const d
   if (!h || !h->s || !ticket || nnz < 0 || k < 1 || k > GM_MAX_K) return GM_EINVAL;
   if (nnz > 0 && (!ids || !w)) return GM_EINVAL;
   Server& S = *h->s;
-  if (nnz > S.cfg.max_batch_nnz) return GM_EINVAL;  // a single launch could not hold it
+  if (nnz > 0x7FFFFFFFll) return GM_EINVAL;  // one launch holds at most 2^31 - 1 elements (a larger
+                                             // request runs alone in its batch)
   bool pinned = false;
   if (!S.fake && nnz > 0) {
     cudaPointerAttributes pa, pb;
@@ -925,6 +934,8 @@ extern "C" int gm_server_stats_get(gm_server* h, gm_server_stats* out) {
   for (const auto& kv : S.reqs) q += kv.second.state == gm::srv::QUEUED;
   out->queued = q;
   out->in_flight_batches = (uint64_t)S.in_flight;
+  out->pack_ns = S.pack_ns_acc.load();
+  out->launch_ns = S.launch_ns_acc.load();
   return GM_OK;
 }
 

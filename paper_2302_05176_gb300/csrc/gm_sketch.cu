@@ -93,6 +93,9 @@ struct SketchArgs {
   float q1, q2, q_split;  // normalised bounds: first pass, later passes, long rows (inf = none)
   const float* t_row;     // learned first-pass bound per row (absolute), or null
   float light_max, medium_max, heavy_max;  // routing thresholds (expected arrivals below T)
+  const int32_t* init_s;  // stream mode (one row): registers start from this sketch, else unfilled
+  const double* init_y;
+  const double* r_row;    // budget pass (plain kernel): FastSearch's R per row, else null
 };
 
 struct SmemScalars {
@@ -100,6 +103,7 @@ struct SmemScalars {
   float red_f[WARPS];
   int red_i[WARPS];
   unsigned long long red_u[WARPS];
+  double red_d[WARPS];
   unsigned long long clk[WARPS][NCLK];  // light, 8-lane, 32-lane, dense, barrier wait, setup, finish, total
 };
 __shared__ SmemScalars sh_scalars;
@@ -426,11 +430,34 @@ __device__ __forceinline__ void reset_lists(SmemScalars& sh) {
   }
 }
 
-__device__ __forceinline__ void init_regs(Reg* regs, int k) {
+__device__ __forceinline__ void init_regs(const SketchArgs& a, Reg* regs, int k) {
   for (int j = threadIdx.x; j < k; j += BLOCK) {
-    regs[j].y = INF_BITS;
-    regs[j].id = UNFILLED_ID;
+    if (a.init_y) {  // a running sketch: (+inf, -1) is an unfilled register
+      regs[j].y = (uint64_t)__double_as_longlong(a.init_y[j]);
+      regs[j].id = a.init_s[j] < 0 ? UNFILLED_ID : (uint64_t)(uint32_t)a.init_s[j];
+    } else {
+      regs[j].y = INF_BITS;
+      regs[j].id = UNFILLED_ID;
+    }
   }
+}
+
+// A row's first-pass bound from the per-row table: an absolute bound, or (when
+// negative) none given, so the closed form applies.
+__device__ __forceinline__ bool row_bound(const SketchArgs& a, int row, float& Tf) {
+  if (!a.t_row) return false;
+  const float t = __ldg(&a.t_row[row]);
+  if (!(t >= 0.0f)) return false;
+  Tf = t;
+  return true;
+}
+
+// The bound of every chunk of a long row (from the row's sum, or the table).
+__device__ __forceinline__ void chunk_bound(const SketchArgs& a, int row, float sum, uint64_t& Tbits, float& Tf) {
+  if (!row_bound(a, row, Tf)) Tf = a.q_split / sum;
+  const bool none = !(Tf < 3.0e38f);
+  Tbits = none ? DBL_MAX_BITS : (uint64_t)__double_as_longlong(f64_from_f32(Tf));
+  if (none) Tf = __int_as_float(0x7F800000);
 }
 
 __device__ __forceinline__ void write_out(const SketchArgs& a, int row, const Reg* regs) {
@@ -452,6 +479,25 @@ __device__ __forceinline__ void row_bounds(const SketchArgs& a, int row, int64_t
   h = h < l ? l : (h > a.nnz ? a.nnz : h);
   lo = l;
   hi = h;
+}
+
+// FP64 sum of the positive weights of [lo, lo+n): per-thread strided sums, warp
+// butterflies, then the warps in order.  Block-wide (two barriers).
+template <int NT>
+__device__ __forceinline__ double block_dsum(const double* w, int64_t lo, int n, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const double v = w[lo + i];
+    if (positive_finite(v)) s += v;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(FULL, s, d);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int q = 0; q < NT / 32; ++q) t += red[q];
+  __syncthreads();
+  return t;
 }
 
 // Sum of the positive weights of [lo, lo+n) (FP32 from bits, Kahan) and their count;
@@ -576,7 +622,8 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
   block_sum<BLOCK>(a, lo, n, sh.red_f, sh.red_i, sumv, npos);
   clk_add(cnt, CLK_SETUP, t);
   for (int pass = first_pass; npos > 0; ++pass) {
-    float Tf = pass == 0 ? (a.t_row ? __ldg(&a.t_row[row]) : a.q1 / sumv) : a.q2 / sumv;
+    float Tf = a.q2 / sumv;
+    if (pass == 0 && !row_bound(a, row, Tf)) Tf = a.q1 / sumv;
     double Td = 0.0;
     bool last = !(Tf < 3.0e38f) || pass >= 12;
     if (!last) {
@@ -597,8 +644,10 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
     __syncthreads();
     clk_add(cnt, CLK_WAIT, t);
     warp_phases<ARITH>(a, lo, Tbits, regs, area, dense, sh, cnt, gave_up, t);
+    // a register above T may still be lowered by an arrival above T: redo wider.
+    // (Without a starting sketch that is exactly an unfilled register.)
     int empty = 0;
-    for (int j = tid; j < a.k; j += BLOCK) empty |= (regs[j].y == INF_BITS);
+    for (int j = tid; j < a.k; j += BLOCK) empty |= (regs[j].y > Tbits);
     const bool again = __syncthreads_or(empty) && !last;
     clk_add(cnt, CLK_FINISH, t);
     if (!again) break;
@@ -616,8 +665,11 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
 __device__ __forceinline__ void finish_long(const SketchArgs& a, int row, int longi, SmemScalars& sh) {
   const int k = a.k;
   const Reg* g = a.long_regs + (int64_t)longi * k;
+  uint64_t Tbits;
+  float Tf;
+  chunk_bound(a, row, a.longs[longi].sum, Tbits, Tf);
   int empty = 0;
-  for (int j = threadIdx.x; j < k; j += BLOCK) empty |= (__ldcg(&g[j].y) == INF_BITS);
+  for (int j = threadIdx.x; j < k; j += BLOCK) empty |= (__ldcg(&g[j].y) > Tbits);
   const bool any_empty = __syncthreads_or(empty) != 0;
   const bool has_pos = a.longs[longi].npos > 0;
   if (any_empty && has_pos && isfinite(a.q_split)) {
@@ -672,7 +724,7 @@ __global__ void __launch_bounds__(BLOCK, 2) fastgm_kernel(SketchArgs a) {
     }
     int64_t lo, hi;
     row_bounds(a, row, lo, hi);
-    init_regs(regs, k);
+    init_regs(a, regs, k);
     if (longi < 0) {  // the whole row in this CTA
       fastgm_row<ARITH>(a, row, lo, (int)(hi - lo), MODE == MODE_ESC ? 1 : 0, regs, area, dense, wbuf, sh, cnt,
                         gave_up);
@@ -684,10 +736,9 @@ __global__ void __launch_bounds__(BLOCK, 2) fastgm_kernel(SketchArgs a) {
     const int64_t chi = min(hi, clo + SPLIT_LEN);
     const LongRow lr = a.longs[longi];
     if (lr.npos > 0 && chi > clo) {
-      float Tf = a.t_row ? __ldg(&a.t_row[row]) : a.q_split / lr.sum;
-      const bool none = !(Tf < 3.0e38f);
-      const uint64_t Tbits = none ? DBL_MAX_BITS : (uint64_t)__double_as_longlong(f64_from_f32(Tf));
-      if (none) Tf = __int_as_float(0x7F800000);
+      uint64_t Tbits;
+      float Tf;
+      chunk_bound(a, row, lr.sum, Tbits, Tf);
       reset_lists(sh);
       __syncthreads();
       long long t = read_clock();
@@ -741,7 +792,7 @@ __global__ void __launch_bounds__(BLOCK, 1) plain_kernel(SketchArgs a) {
     resolve_unit(a, u, n_extra, n_long, row, chunk, longi);
     int64_t lo, hi;
     row_bounds(a, row, lo, hi);
-    init_regs(regs, k);
+    init_regs(a, regs, k);
     const int64_t clo = longi < 0 ? lo : lo + (int64_t)chunk * SPLIT_LEN;
     const int64_t chi = longi < 0 ? hi : min(hi, clo + SPLIT_LEN);
     const int n = (int)(chi - clo);
@@ -749,6 +800,13 @@ __global__ void __launch_bounds__(BLOCK, 1) plain_kernel(SketchArgs a) {
       float sumv;
       int npos;
       block_sum<BLOCK>(a, lo, n, sh.red_f, sh.red_i, sumv, npos);  // validation only
+    }
+    // budget pass (FastSearch, Algorithm 1): element i releases ceil(R v_i / sum v)
+    // of its arrivals, the ratio and product in FP64 as the paper's schedule states
+    double Rr = 0.0, dsum = 0.0;
+    if (a.r_row) {
+      Rr = a.r_row[row];
+      dsum = longi < 0 ? block_dsum<BLOCK>(a.w, lo, n, sh.red_d) : __ldcg(&a.longs[longi].dsum);
     }
     if (tid == 0) sh.pool = 0;
     __syncthreads();
@@ -762,12 +820,17 @@ __global__ void __launch_bounds__(BLOCK, 1) plain_kernel(SketchArgs a) {
       if (lane == 0) ++cnt.elements;
       const int32_t id = a.ids[clo + slot];
       const double R = arr_rcp<ARITH>(v);
+      int lim = k;
+      if (a.r_row) {
+        const double b = ceil(__dmul_rn(Rr, __ddiv_rn(v, dsum)));
+        lim = b < (double)k ? (int)b : k;
+      }
       dp.reset(k, lane);
       Fix carry = fix_zero();
-      for (int z0 = 0; z0 < k; z0 += 32) {  // all k arrivals, 32 per step
+      for (int z0 = 0; z0 < lim; z0 += 32) {  // all k arrivals (or the budget), 32 per step
         int J, c;
         const uint64_t bb = warp_batch<ARITH>(id, R, z0, k, a.key0, a.key1, a.ctab, carry, lane, J);
-        const int nz = min(32, k - z0);
+        const int nz = min(32, lim - z0);
         if (lane == 0) cnt.arrivals += (uint32_t)nz;
         warp_fy_steps(dp, z0, J, nz, lane, c);
         if (lane < nz && bb <= DBL_MAX_BITS) {
@@ -839,7 +902,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(SketchArgs a) {
         lr.done = 0u;
         lr.sum = 0.0f;
         lr.npos = 0;
-        lr.pad[0] = lr.pad[1] = 0u;
+        lr.dsum = 0.0;
         a.longs[i] = lr;
       }
     }
@@ -878,13 +941,20 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(SketchArgs a) {
 __global__ void __launch_bounds__(256) longprep_kernel(SketchArgs a) {
   __shared__ float red_f[8];
   __shared__ int red_i[8];
+  __shared__ double red_d[8];
   const uint32_t n_long = a.hdr->n_long, n_extra = a.hdr->n_extra;
   const uint32_t n_chunks = n_long + n_extra;
   const int k = a.k;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < (int64_t)n_long * k;
        j += (int64_t)gridDim.x * blockDim.x) {
-    a.long_regs[j].y = INF_BITS;
-    a.long_regs[j].id = UNFILLED_ID;
+    const int r = (int)(j % k);
+    if (a.init_y) {  // stream mode: the one row starts from the running sketch
+      a.long_regs[j].y = (uint64_t)__double_as_longlong(a.init_y[r]);
+      a.long_regs[j].id = a.init_s[r] < 0 ? UNFILLED_ID : (uint64_t)(uint32_t)a.init_s[r];
+    } else {
+      a.long_regs[j].y = INF_BITS;
+      a.long_regs[j].id = UNFILLED_ID;
+    }
   }
   // SUB pieces per chunk, so that enough CTAs stream each long row
   constexpr int SUB = 8, PIECE = SPLIT_LEN / SUB;
@@ -907,9 +977,12 @@ __global__ void __launch_bounds__(256) longprep_kernel(SketchArgs a) {
     float s;
     int np;
     block_sum<256>(a, clo, (int)(chi - clo), red_f, red_i, s, np);
+    double ds = 0.0;
+    if (a.r_row) ds = block_dsum<256>(a.w, clo, (int)(chi - clo), red_d);
     if (threadIdx.x == 0) {
       atomicAdd(&a.longs[longi].sum, s);
       atomicAdd(&a.longs[longi].npos, np);
+      if (a.r_row) atomicAdd(&a.longs[longi].dsum, ds);
     }
   }
 }
@@ -997,7 +1070,8 @@ static gm_tuning tuning_for(int k, int32_t n_rows, int64_t nnz) {
 static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
                                int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out,
                                void* workspace, size_t workspace_bytes, cudaStream_t stream, bool plain,
-                               const float* t_row, const gm_tuning* tuning);
+                               const float* t_row, const gm_tuning* tuning, const int32_t* init_s = nullptr,
+                               const double* init_y = nullptr, const double* r_row = nullptr);
 
 int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
                   int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
@@ -1009,8 +1083,10 @@ int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, i
 static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
                                int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out,
                                void* workspace, size_t workspace_bytes, cudaStream_t stream, bool plain,
-                               const float* t_row, const gm_tuning* tuning) {
+                               const float* t_row, const gm_tuning* tuning, const int32_t* init_s,
+                               const double* init_y, const double* r_row) {
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K) return GM_EINVAL;
+  if (init_y && (n_rows != 1 || plain)) return GM_EINVAL;
   if (nnz > 0x7FFFFFFFll) return GM_EINVAL;
   if (!workspace || !row_ptr || (n_rows > 0 && (!s_out || !y_out)) || (nnz > 0 && (!ids || !w)))
     return GM_EINVAL;
@@ -1047,6 +1123,9 @@ static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const
   a.esc = L.esc;
   a.max_long = (int)L.max_long;
   a.t_row = plain ? nullptr : t_row;
+  a.init_s = init_s;
+  a.init_y = init_y;
+  a.r_row = plain ? r_row : nullptr;
   const gm_tuning tn = tuning ? *tuning : tuning_for(k, n_rows, nnz);
   if (!tuning_ok(tn)) return GM_EINVAL;
   a.light_max = tn.light_max;
@@ -1236,6 +1315,157 @@ extern "C" int gm_tune(const int64_t* row_ptr, const int32_t* ids, const double*
   *best = cur;
   if (best_ms) *best_ms = t_cur;
   return GM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stream-FastGM (Algorithm 2): chunks of a stream folded into a running sketch.
+// ---------------------------------------------------------------------------
+namespace gm {
+
+// row_ptr = {0, n}; the chunk's first-pass bound: the running sketch's y* rounded
+// up to FP32 once every register is filled (an arrival above it cannot lower any
+// register), else -1 (the closed form of the chunk applies).
+__global__ void stream_prep_kernel(const double* __restrict__ y, int k, int64_t n, int64_t* row_ptr, float* t_row) {
+  __shared__ unsigned long long red[8];
+  unsigned long long m = 0ull;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(y[j]);
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(FULL, m, d);
+    m = o > m ? o : m;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = red[q] > m ? red[q] : m;
+    row_ptr[0] = 0;
+    row_ptr[1] = n;
+    const double ys = __longlong_as_double((long long)m);
+    // rounded up, and at least the smallest normal float (a larger bound is always safe)
+    t_row[0] = (m >= INF_BITS) ? -1.0f : fmaxf(__double2float_ru(ys), 1.17549435e-38f);
+  }
+}
+
+__global__ void stream_reset_kernel(int32_t* s, double* y, int k) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < k) {
+    s[j] = -1;
+    y[j] = __longlong_as_double((long long)INF_BITS);
+  }
+}
+
+}  // namespace gm
+
+extern "C" size_t gm_stream_workspace_bytes(int64_t n, int32_t k) {
+  if (n < 0 || k < 1 || k > GM_MAX_K) return 0;
+  return gm::ws_bytes(1, n, k) + 256;
+}
+
+extern "C" int gm_stream_reset(int32_t* s, double* y, int32_t k, void* stream) {
+  if (!s || !y || k < 1 || k > GM_MAX_K) return GM_EINVAL;
+  gm::stream_reset_kernel<<<(k + 255) / 256, 256, 0, (cudaStream_t)stream>>>(s, y, k);
+  return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
+}
+
+extern "C" int gm_stream_ingest(int32_t* s, double* y, int32_t k, const int32_t* ids, const double* w, int64_t n,
+                                uint64_t seed, uint32_t flags, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!s || !y || k < 1 || k > GM_MAX_K || n < 0 || n > 0x7FFFFFFFll || (n > 0 && (!ids || !w)) || !workspace)
+    return GM_EINVAL;
+  if ((flags & GM_BOUND_MASK) == GM_BOUND_LEARNED) return GM_EINVAL;
+  const size_t base = gm::ws_bytes(1, n, k);
+  if (workspace_bytes < gm_stream_workspace_bytes(n, k)) return GM_ENOMEM;
+  if (n == 0) return GM_OK;
+  unsigned char* extra = static_cast<unsigned char*>(workspace) + base;
+  int64_t* row_ptr = reinterpret_cast<int64_t*>(extra);
+  float* t_row = reinterpret_cast<float*>(extra + 16);
+  const cudaStream_t st = (cudaStream_t)stream;
+  gm::stream_prep_kernel<<<1, 256, 0, st>>>(y, k, n, row_ptr, t_row);
+  if (cudaGetLastError() != cudaSuccess) return GM_ECUDA;
+  return gm::launch_sketch_tuned(row_ptr, ids, w, 1, n, k, seed, flags, s, y, workspace, base, st, false, t_row,
+                                 nullptr, s, y);
+}
+
+// ---------------------------------------------------------------------------
+// FastSearch's budgets (Algorithm 1) and caller-given bounds.
+// ---------------------------------------------------------------------------
+namespace gm {
+
+// Per-row bounds given as doubles -> the sketch's FP32 first-pass bounds, rounded
+// up (a larger bound is always safe): > 0 and finite: that bound; +inf: none;
+// otherwise (<= 0, NaN): -1, the closed form.
+__global__ void bound_prep_kernel(const double* __restrict__ b, int n, float* t_row) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const double x = b[r];
+  float t = -1.0f;
+  if (x > 0.0) t = isinf(x) ? __int_as_float(0x7F800000) : fmaxf(__double2float_ru(x), 1.17549435e-38f);
+  t_row[r] = t;
+}
+
+// The largest register of each row (+inf if one is unfilled), one warp per row.
+__global__ void row_ystar_kernel(const double* __restrict__ y, int n_rows, int k, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= n_rows) return;
+  unsigned long long m = 0ull;
+  for (int j = lane; j < k; j += 32) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(y[r * k + j]);
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(FULL, m, d);
+    m = o > m ? o : m;
+  }
+  if (lane == 0) out[r] = __longlong_as_double((long long)m);
+}
+
+}  // namespace gm
+
+extern "C" int gm_sketch_budget(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
+                                int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, const double* R_row,
+                                int32_t* s_out, double* y_out, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!R_row && n_rows > 0) return GM_EINVAL;
+  return gm::launch_sketch_tuned(row_ptr, ids, w, n_rows, nnz, k, seed,
+                                 flags & (GM_FLAG_VALIDATE | GM_FLAG_FP64_UNIT | GM_FLAG_INT_PRODUCTS), s_out, y_out,
+                                 workspace, workspace_bytes, (cudaStream_t)stream, true, nullptr, nullptr, nullptr,
+                                 nullptr, R_row);
+}
+
+extern "C" size_t gm_sketch_bounded_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k) {
+  const size_t base = gm_sketch_workspace_bytes(n_rows, nnz, k, 0u);
+  return base ? base + gm::round_up((size_t)(n_rows > 0 ? n_rows : 0) * 4, 256) : 0;
+}
+
+extern "C" int gm_sketch_bounded(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
+                                 int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, const double* bound_row,
+                                 int32_t* s_out, double* y_out, void* workspace, size_t workspace_bytes,
+                                 void* stream) {
+  if (n_rows < 0 || (n_rows > 0 && !bound_row) || !workspace) return GM_EINVAL;
+  if ((flags & GM_BOUND_MASK) == GM_BOUND_LEARNED) return GM_EINVAL;
+  const size_t need = gm_sketch_bounded_workspace_bytes(n_rows, nnz, k);
+  if (need == 0) return GM_EINVAL;
+  if (workspace_bytes < need) return GM_ENOMEM;
+  const size_t base = gm_sketch_workspace_bytes(n_rows, nnz, k, 0u);
+  float* t_row = reinterpret_cast<float*>(static_cast<unsigned char*>(workspace) + base);
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (n_rows > 0) {
+    gm::bound_prep_kernel<<<(n_rows + 255) / 256, 256, 0, st>>>(bound_row, n_rows, t_row);
+    if (cudaGetLastError() != cudaSuccess) return GM_ECUDA;
+  }
+  return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags, s_out, y_out, workspace, base, st, false,
+                           n_rows > 0 ? t_row : nullptr);
+}
+
+extern "C" int gm_row_ystar(const double* y, int32_t n_rows, int32_t k, double* out, void* stream) {
+  if (n_rows < 0 || k < 1 || (n_rows > 0 && (!y || !out))) return GM_EINVAL;
+  if (n_rows == 0) return GM_OK;
+  const int64_t threads = (int64_t)n_rows * 32;
+  gm::row_ystar_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, (cudaStream_t)stream>>>(y, n_rows, k, out);
+  return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
 }
 
 // ---------------------------------------------------------------------------

@@ -104,6 +104,18 @@ def lib():
         L.gm_tuning_get.argtypes = [ctypes.c_int32, ctypes.c_int64, tp]
         L.gm_tuning_save.argtypes = [ctypes.c_char_p]
         L.gm_tuning_load.argtypes = [ctypes.c_char_p]
+        L.gm_stream_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int32]
+        L.gm_stream_workspace_bytes.restype = ctypes.c_size_t
+        L.gm_stream_reset.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
+        L.gm_stream_ingest.argtypes = [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_int64, ctypes.c_uint64,
+                                       ctypes.c_uint32, _vp, ctypes.c_size_t, _vp]
+        L.gm_sketch_budget.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                       ctypes.c_uint32, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+        L.gm_sketch_bounded_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
+        L.gm_sketch_bounded_workspace_bytes.restype = ctypes.c_size_t
+        L.gm_sketch_bounded.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.c_uint32, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+        L.gm_row_ystar.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
         L.gm_strerror.argtypes = [ctypes.c_int]
         L.gm_strerror.restype = ctypes.c_char_p
         L.gm_version.restype = ctypes.c_char_p
@@ -427,3 +439,59 @@ def tuning_save(path):
 
 def tuning_load(path):
     _check(lib().gm_tuning_load(os.fsencode(path)), "gm_tuning_load")
+
+
+# --- Stream-FastGM (gm_stream_*) ------------------------------------------------------------------
+
+class StreamSketch:
+    """A running sketch fed chunk by chunk (Algorithm 2): s, y are device tensors [k]."""
+
+    def __init__(self, k, seed, flags=0, device=None, stream=None):
+        dev = device or torch.device("cuda")
+        self.k, self.seed, self.flags = int(k), int(seed), int(flags)
+        self.s = torch.empty(self.k, dtype=torch.int32, device=dev)
+        self.y = torch.empty(self.k, dtype=torch.float64, device=dev)
+        self.ws = torch.empty(0, dtype=torch.uint8, device=dev)
+        _check(lib().gm_stream_reset(_ptr(self.s), _ptr(self.y), self.k, _stream_handle(stream)), "gm_stream_reset")
+
+    def ingest(self, ids, w, stream=None):
+        _need_cuda(ids, torch.int32, "ids")
+        _need_cuda(w, torch.float64, "w")
+        n = ids.numel()
+        need = lib().gm_stream_workspace_bytes(n, self.k)
+        if need == 0:
+            raise GmError(GM_EINVAL, "gm_stream_workspace_bytes")
+        if self.ws.numel() < need:
+            self.ws = torch.empty(need, dtype=torch.uint8, device=self.s.device)
+        _check(lib().gm_stream_ingest(_ptr(self.s), _ptr(self.y), self.k, _ptr(ids), _ptr(w), n,
+                                      self.seed & 0xFFFFFFFFFFFFFFFF, self.flags, _ptr(self.ws), self.ws.numel(),
+                                      _stream_handle(stream)), "gm_stream_ingest")
+        return self
+
+
+# --- FastSearch's budgets and caller-given bounds --------------------------------------------------
+
+def gm_sketch_budget(row_ptr, ids, w, k, seed, R_row, flags=0, s_out=None, y_out=None, ws=None, stream=None):
+    """Release min(k, ceil(R_row[r] v_i / sum v)) arrivals of each element (FastSearch's step)."""
+    _need_cuda(R_row, torch.float64, "R_row")
+    fn = lambda *a: lib().gm_sketch_budget(*a[:8], _ptr(R_row), *a[8:])
+    return _sketch(fn, "gm_sketch_budget", row_ptr, ids, w, k, seed, flags, s_out, y_out, ws, stream)
+
+
+def gm_sketch_bounded(row_ptr, ids, w, k, seed, bound_row, flags=0, s_out=None, y_out=None, ws=None, stream=None):
+    """FastGM with the caller's first-pass bound per row (device doubles)."""
+    _need_cuda(bound_row, torch.float64, "bound_row")
+    n_rows, nnz = row_ptr.numel() - 1, ids.numel()
+    if ws is None:
+        ws = torch.empty(lib().gm_sketch_bounded_workspace_bytes(n_rows, nnz, int(k)), dtype=torch.uint8,
+                         device=row_ptr.device)
+    fn = lambda *a: lib().gm_sketch_bounded(*a[:8], _ptr(bound_row), *a[8:])
+    return _sketch(fn, "gm_sketch_bounded", row_ptr, ids, w, k, seed, flags, s_out, y_out, ws, stream)
+
+
+def gm_row_ystar(y, out=None, stream=None):
+    _need_cuda(y, torch.float64, "y")
+    n, k = y.shape
+    out = torch.empty(n, dtype=torch.float64, device=y.device) if out is None else out
+    _check(lib().gm_row_ystar(_ptr(y), n, k, _ptr(out), _stream_handle(stream)), "gm_row_ystar")
+    return out

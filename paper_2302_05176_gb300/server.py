@@ -19,7 +19,8 @@ class Config(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_size_t), ("staging_bytes", ctypes.c_size_t),
                 ("max_batch_nnz", ctypes.c_int64), ("max_batch_rows", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint32),
-                ("params", _vp), ("margin", ctypes.c_float), ("fake_device", ctypes.c_int32)]
+                ("params", _vp), ("margin", ctypes.c_float), ("stage_pinned", ctypes.c_int32),
+                ("fake_device", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -35,7 +36,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "submitted", "finished", "cancelled", "refused", "failed", "sketch_batches", "query_batches",
         "sketch_rows", "sketch_elements", "queries", "arena_bytes", "arena_peak_bytes", "arena_resident_bytes",
-        "queued", "in_flight_batches")]
+        "queued", "in_flight_batches", "staged_requests", "direct_requests", "pack_ns", "launch_ns")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -75,8 +76,8 @@ def now_ns():
 class Server:
     """A serving engine on the current CUDA device (or a fake device)."""
 
-    def __init__(self, device_bytes=8 << 30, staging_bytes=64 << 20, max_batch_nnz=1 << 26, max_batch_rows=4096,
-                 n_streams=2, seed=1, flags=0, params=None, margin=0.0, fake_device=False):
+    def __init__(self, device_bytes=8 << 30, staging_bytes=64 << 20, max_batch_nnz=1 << 23, max_batch_rows=4096,
+                 n_streams=4, seed=1, flags=0, params=None, margin=0.0, stage_pinned=False, fake_device=False):
         L = _lib()
         cfg = Config()
         L.gm_server_config_default(ctypes.byref(cfg))
@@ -86,6 +87,7 @@ class Server:
         self._params = params  # keep the model alive
         cfg.params = _vp(params.data_ptr()) if params is not None else _vp(0)
         cfg.margin = float(margin)
+        cfg.stage_pinned = 1 if stage_pinned else 0
         cfg.fake_device = 1 if fake_device else 0
         h = _vp()
         gm._check(L.gm_server_create(ctypes.byref(cfg), ctypes.byref(h)), "gm_server_create")
