@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--flags", type=int, default=0, help="gm_sketch flags of the --only fastgm step")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-bound ablation")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
+    ap.add_argument("--no-pareto", action="store_true", help="skip the heavy-tail (Pareto, k=4096) leg")
     ap.add_argument("--no-tune", action="store_true", help="time the default tuning instead of gm_tune's")
     ap.add_argument("--tuning-file", default=None, help="load the tuning table from this file if it exists, "
                     "else tune and save it there")
@@ -57,6 +58,8 @@ def parse():
     ap.add_argument("--serve-stage-pinned", action="store_true")
     ap.add_argument("--learned-rows", type=int, default=200_000, help="sketches in the bound network's training set")
     ap.add_argument("--learned-steps", type=int, default=400, help="Adam steps of the bound network")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="the paper's synthetic accuracy experiments on the GPU sketches (Task 1 / Task 2 RMSE)")
     ap.add_argument("--arith", action="store_true",
                     help="time the per-arrival arithmetic: FP64 unit vs integer pipes (diagnostic kernels)")
     return ap.parse_args()
@@ -313,6 +316,12 @@ def main():
         return run_reference(args)
     if args.arith:
         return run_arith(args)
+    if args.accuracy:
+        import torch
+        from paper_2302_05176_gb300 import accuracy
+        print(json.dumps({"task1_jaccard": accuracy.jaccard_rmse(), "task2_cardinality": accuracy.cardinality_rmse()}),
+              flush=True)
+        return
     if args.serve_only:
         import torch
         from paper_2302_05176_gb300 import gm
@@ -470,6 +479,8 @@ def main():
         "clocks": clk,
     }
     line["graph"] = graph_leg(args, timed, sketch_call, ms_main, (rp, ids, w))
+    if not args.no_pareto:
+        line["pareto_k4096"] = pareto_leg(args)
     if not args.no_learned:
         line["learned_k1024"] = learned_ablation(args, timed, sketch_call, (rp, ids, w), s_main, y_main, ms_main,
                                                  st_main, n_rows)
@@ -481,6 +492,49 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def pareto_leg(args):
+    """Heavy-tail stress: 16 vectors of n+ = 10^6, Pareto(1.2, x_min 1e-3) weights,
+    k = 4096: FastGM with the closed-form bound (tuned), FastGM with no initial
+    bound, the plain sketch; arrivals generated per element and HBM GB/s."""
+    import torch
+    from paper_2302_05176_gb300 import gm
+    from paper_2302_05176_gb300 import workloads as W
+    X = W.pareto_heavy(seed=SEED, n_rows=16, n_pos=1_000_000)
+    rp, ids, w = gm.to_device(X)
+    k = 4096
+    if not args.no_tune:
+        gm.gm_tune(rp, ids, w, k, SEED)
+    out = {"workload": "pareto_heavy: 16 rows x 1e6 elements, Pareto(1.2, x_min 1e-3), k=4096, seed=1",
+           "nnz": X.nnz}
+    ref = None
+    for name, fn, flags, steps in (("fastgm", gm.gm_sketch, 0, max(3, args.steps // 3)),
+                                   ("fastgm_no_bound", gm.gm_sketch, gm.GM_BOUND_NONE, 1),
+                                   ("plain", gm.gm_sketch_plain, 0, 1)):
+        s_o = torch.empty((X.n_rows, k), dtype=torch.int32, device="cuda")
+        y_o = torch.empty((X.n_rows, k), dtype=torch.float64, device="cuda")
+        ws = gm.workspace(X.n_rows, X.nnz, k)
+        fn(rp, ids, w, k, SEED, flags=flags, s_out=s_o, y_out=y_o, ws=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn(rp, ids, w, k, SEED, flags=flags, s_out=s_o, y_out=y_o, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        _, st = gm.gm_status(ws)
+        if ref is None:
+            ref = (s_o.clone(), y_o.clone())
+        same = bool(torch.equal(s_o, ref[0]) and torch.equal(y_o.view(torch.int64), ref[1].view(torch.int64)))
+        out[name] = {"ms_per_step": ms, "sketches_per_s": X.n_rows / (ms * 1e-3),
+                     "elements_per_s": X.nnz / (ms * 1e-3), "arrivals_per_element": st["arrivals"] / X.nnz,
+                     "hbm_gbs": algorithmic_bytes(X.nnz, X.n_rows, k) / (ms * 1e-3) / 1e9,
+                     "identical_to_fastgm": same}
+    out["speedup_vs_plain"] = out["plain"]["ms_per_step"] / out["fastgm"]["ms_per_step"]
+    out["speedup_vs_no_bound"] = out["fastgm_no_bound"]["ms_per_step"] / out["fastgm"]["ms_per_step"]
+    return out
 
 
 def graph_leg(args, timed, sketch_call, ms_main, dev_csr):
