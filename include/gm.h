@@ -348,6 +348,22 @@ int gm_stream_reset(int32_t* s, double* y, int32_t k, void* stream);
 int gm_stream_ingest(int32_t* s, double* y, int32_t k, const int32_t* ids, const double* w, int64_t n, uint64_t seed,
                      uint32_t flags, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---- host-memory batches ---------------------------------------------------------
+ * gm_sketch over a CSR batch in HOST memory (row_ptr, ids, w, s_out, y_out all
+ * host arrays; page-locked ones are copied asynchronously, pageable ones through
+ * the driver's staging).  The batch is cut into chunks of rows (at least 512,
+ * about a quarter of the batch) that are copied to the device, sketched and
+ * copied back on two streams, so the copies of one chunk overlap the sketch of
+ * another.  Blocks until every register is in s_out / y_out.  The same registers
+ * as gm_sketch on the whole batch.  row_ptr is checked on the host (GM_EINVAL:
+ * row_ptr[0] != 0, decreasing, row_ptr[n_rows] != nnz).  workspace: device memory
+ * of gm_sketch_host_workspace_bytes(n_rows, nnz, k) bytes.  Concurrent calls in
+ * one process are serialised. */
+size_t gm_sketch_host_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k);
+int gm_sketch_host(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
+                   int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
+                   size_t workspace_bytes);
+
 /* ---- CUDA graphs --------------------------------------------------------------
  * Not in the paper.  A gm_sketch call is five kernel launches plus host-side
  * setup; for a workload repeated over the same buffers (a fixed-shape batch

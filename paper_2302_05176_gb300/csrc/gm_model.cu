@@ -147,42 +147,167 @@ __device__ __forceinline__ int weight_bin(uint64_t bits) {
   return b < BIN_MIN ? BIN_MIN : (b > BIN_MIN + NBINS - 1 ? BIN_MIN + NBINS - 1 : b);
 }
 
+// Sum of positive doubles in FP32 with a running power-of-two scale: the sum is
+// (s - c) 2^(e - 1023), s a Kahan sum, c its compensation, e the largest biased
+// exponent seen.  Each term is its double rounded to 24 bits and scaled from the
+// bits (no FP64 instruction per element); terms below 2^-126 of the largest are
+// dropped.  Relative error about 2^-24: ample for an FP32 feature.
+struct ScaledSum {
+  int e;
+  float s, c;
+};
+__device__ __forceinline__ float pow2f(int d) { return d < -126 ? 0.0f : __int_as_float((d + 127) << 23); }
+__device__ __forceinline__ void ssum_add(ScaledSum& a, uint64_t bits) {
+  int e = (int)(bits >> 52);
+  uint64_t f = bits & 0x000FFFFFFFFFFFFFull;
+  if (e == 0) {  // subnormal: normalise the fraction
+    const int sh = __clzll((long long)f) - 11;
+    f = (f << sh) & 0x000FFFFFFFFFFFFFull;
+    e = 1 - sh;
+  }
+  uint32_t m = (uint32_t)(f >> 29) + (uint32_t)((f >> 28) & 1ull);  // 23 fraction bits, rounded
+  if (m >> 23) {  // rounding carried into the exponent
+    m = 0u;
+    ++e;
+  }
+  if (e > a.e) {
+    const float sc = pow2f(a.e - e);
+    a.s *= sc;
+    a.c *= sc;
+    a.e = e;
+  }
+  const int d = e - a.e;
+  if (d < -126) return;
+  const float t = __int_as_float(((d + 127) << 23) | (int)m);
+  const float y = t - a.c;
+  const float u = a.s + y;
+  a.c = (u - a.s) - y;
+  a.s = u;
+}
+__device__ __forceinline__ double ssum_value(const ScaledSum& a) {
+  return a.e < -100000 ? 0.0 : ldexp((double)(a.s - a.c), a.e - 1023);
+}
+
 struct FeatSmem {
-  int hist[NW][NBINS];  // one histogram per warp: fewer lanes contend for a bin
+  int hist[NW][NBINS];  // one histogram per warp: a warp's own row, or a share of a long row
+  float feat[NW][F];
   int red_i[NW];
-  double red_s[NW], red_m[NW];
+  double red_s[NW];
+  unsigned long long red_m[NW];
   int scan[NW];
   int qbin[4];
 };
 
-// Features of row [lo, hi) into feat[8] (shared), by the whole block.
-__device__ void row_features(const double* __restrict__ w, int64_t lo, int64_t hi, int k, FeatSmem& sm,
-                             float* feat) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int b = tid; b < NW * NBINS; b += NT) (&sm.hist[0][0])[b] = 0;
-  __syncthreads();
-  // Four loads in flight per thread.
+// Accumulate elements [lo, hi) with stride `stride` from `first` into (np, sum,
+// max bits, histogram); four loads in flight per thread.
+__device__ __forceinline__ void feat_scan(const double* __restrict__ w, int64_t first, int64_t hi, int stride,
+                                          int* hist, int& np, ScaledSum& acc, uint64_t& mxb) {
   constexpr int U = 4;
-  int np = 0;
-  double sum = 0.0;
-  uint64_t mxb = 0ull;  // positive doubles order like their bit patterns
-  for (int64_t base = lo + (tid - lane); base < hi; base += (int64_t)U * NT) {
+  for (int64_t base = first; base < hi; base += (int64_t)U * stride) {
     double v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t i = base + u * NT + lane;
+      const int64_t i = base + (int64_t)u * stride;
       v[u] = i < hi ? __ldg(&w[i]) : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint64_t b = (uint64_t)__double_as_longlong(v[u]);
-      const bool ok = b > 0ull && b < INF_BITS;  // positive and finite
-      np += ok ? 1 : 0;
-      sum += ok ? v[u] : 0.0;
-      mxb = (ok && b > mxb) ? b : mxb;
-      if (ok) atomicAdd(&sm.hist[warp][weight_bin(b) - BIN_MIN], 1);
+      if (b > 0ull && b < INF_BITS) {  // positive and finite
+        ++np;
+        ssum_add(acc, b);
+        mxb = b > mxb ? b : mxb;
+        atomicAdd(&hist[weight_bin(b) - BIN_MIN], 1);
+      }
     }
   }
+}
+
+// The eight features from (np, sum, max, quantile bins).
+__device__ __forceinline__ void write_features(int np, double sum, uint64_t mxb, const int* qbin, int k,
+                                               float* feat) {
+  if (np > 0) {
+    feat[0] = (float)log((double)np);
+    feat[1] = (float)log(sum);
+    feat[2] = (float)log(__longlong_as_double((long long)mxb));
+#pragma unroll
+    for (int qi = 0; qi < 4; ++qi) feat[3 + qi] = (float)(((double)qbin[qi] + 0.5) * (0.69314718055994531 / 4.0));
+  } else {
+#pragma unroll
+    for (int f = 0; f < 7; ++f) feat[f] = 0.0f;
+  }
+  feat[7] = (float)log((double)k);
+}
+
+__device__ __forceinline__ long long quant_rank(int np, int qi) {
+  const long long r = ((long long)np * quant_pct(qi) + 99) / 100;
+  return r < 1 ? 1 : r;
+}
+
+// Features of row [lo, hi) by one warp (rows of up to WARP_ROW_MAX elements):
+// no block barrier.  hist: the warp's NBINS counters; feat: its 8 floats.
+constexpr int64_t WARP_ROW_MAX = 4096;
+__device__ void warp_row_features(const double* __restrict__ w, int64_t lo, int64_t hi, int k, int* hist,
+                                  float* feat) {
+  const int lane = threadIdx.x & 31;
+  for (int b = lane; b < NBINS; b += 32) hist[b] = 0;
+  __syncwarp();
+  int np = 0;
+  ScaledSum acc{-1000000, 0.0f, 0.0f};
+  uint64_t mxb = 0ull;
+  feat_scan(w, lo + lane, hi, 32, hist, np, acc, mxb);
+  double sum = ssum_value(acc);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    np += __shfl_xor_sync(FULL, np, d);
+    sum += __shfl_xor_sync(FULL, sum, d);
+    const uint64_t o = __shfl_xor_sync(FULL, mxb, d);
+    mxb = o > mxb ? o : mxb;
+  }
+  __syncwarp();
+  // lane l owns bins [32 l, 32 l + 32)
+  constexpr int PER = NBINS / 32;
+  int own = 0;
+  for (int q = 0; q < PER; ++q) own += hist[PER * lane + q];
+  int incl = own;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += y;
+  }
+  int qbin[4];
+#pragma unroll
+  for (int qi = 0; qi < 4; ++qi) {
+    const long long r = quant_rank(np, qi);
+    int bin = 0, c = incl - own;
+    bool found = false;  // (bins are signed: found is a flag of its own)
+    if (np > 0 && c < r && incl >= r)
+      for (int q = 0; q < PER; ++q) {
+        c += hist[PER * lane + q];
+        if (c >= r) {
+          bin = BIN_MIN + PER * lane + q;
+          found = true;
+          break;
+        }
+      }
+    const uint32_t who = __ballot_sync(FULL, found);
+    qbin[qi] = who ? __shfl_sync(FULL, bin, __ffs(who) - 1) : 0;
+  }
+  if (lane == 0) write_features(np, sum, mxb, qbin, k, feat);
+  __syncwarp();
+}
+
+// Features of a long row by the whole block (per-warp histograms).
+__device__ void block_row_features(const double* __restrict__ w, int64_t lo, int64_t hi, int k, FeatSmem& sm,
+                                   float* feat) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int b = tid; b < NW * NBINS; b += NT) (&sm.hist[0][0])[b] = 0;
+  __syncthreads();
+  int np = 0;
+  ScaledSum acc{-1000000, 0.0f, 0.0f};
+  uint64_t mxb = 0ull;
+  feat_scan(w, lo + tid, hi, NT, sm.hist[warp], np, acc, mxb);
+  double sum = ssum_value(acc);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
     np += __shfl_xor_sync(FULL, np, d);
@@ -193,18 +318,18 @@ __device__ void row_features(const double* __restrict__ w, int64_t lo, int64_t h
   if (lane == 0) {
     sm.red_i[warp] = np;
     sm.red_s[warp] = sum;
-    sm.red_m[warp] = __longlong_as_double((long long)mxb);
+    sm.red_m[warp] = mxb;
   }
   __syncthreads();
   np = 0;
   sum = 0.0;
-  double mx = 0.0;
+  mxb = 0ull;
   for (int q = 0; q < NW; ++q) {
     np += sm.red_i[q];
     sum += sm.red_s[q];
-    mx = fmax(mx, sm.red_m[q]);
+    mxb = sm.red_m[q] > mxb ? sm.red_m[q] : mxb;
   }
-  // exclusive scan of the histogram: thread t owns bins 4t .. 4t+3
+  // exclusive scan of the merged histogram: thread t owns bins 4t .. 4t+3
   static_assert(NBINS == 4 * NT, "four bins per thread");
   int cnt4[4];
 #pragma unroll
@@ -227,8 +352,7 @@ __device__ void row_features(const double* __restrict__ w, int64_t lo, int64_t h
   for (int q = 0; q < warp; ++q) run += sm.scan[q];
 #pragma unroll
   for (int qi = 0; qi < 4; ++qi) {
-    long long r = ((long long)np * quant_pct(qi) + 99) / 100;
-    if (r < 1) r = 1;
+    const long long r = quant_rank(np, qi);
     int c = run;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -238,19 +362,7 @@ __device__ void row_features(const double* __restrict__ w, int64_t lo, int64_t h
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    if (np > 0) {
-      feat[0] = (float)log((double)np);
-      feat[1] = (float)log(sum);
-      feat[2] = (float)log(mx);
-#pragma unroll
-      for (int qi = 0; qi < 4; ++qi) feat[3 + qi] = (float)(((double)sm.qbin[qi] + 0.5) * (0.69314718055994531 / 4.0));
-    } else {
-#pragma unroll
-      for (int f = 0; f < 7; ++f) feat[f] = 0.0f;
-    }
-    feat[7] = (float)log((double)k);
-  }
+  if (tid == 0) write_features(np, sum, mxb, sm.qbin, k, feat);
   __syncthreads();
 }
 
@@ -262,16 +374,39 @@ __device__ __forceinline__ void clamp_row(const int64_t* row_ptr, int r, int64_t
   hi = h;
 }
 
-__global__ void __launch_bounds__(NT) features_kernel(const int64_t* row_ptr, const double* w, int n_rows,
-                                                      int64_t nnz, int k, float* feats) {
-  __shared__ FeatSmem sm;
-  __shared__ float feat[F];
+// Rows of up to WARP_ROW_MAX elements go to warps (global warp index, strided),
+// longer rows to whole blocks; `emit(row, feat)` runs in the warp (or warp 0 of
+// the block) that computed them.
+template <class EMIT>
+__device__ __forceinline__ void for_each_row_features(const int64_t* row_ptr, const double* w, int n_rows,
+                                                      int64_t nnz, int k, FeatSmem& sm, EMIT emit) {
+  const int warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * NW + warp, nw = (int64_t)gridDim.x * NW;
+  for (int64_t r = gw; r < n_rows; r += nw) {
+    int64_t lo, hi;
+    clamp_row(row_ptr, (int)r, nnz, lo, hi);
+    if (hi - lo > WARP_ROW_MAX) continue;
+    warp_row_features(w, lo, hi, k, sm.hist[warp], sm.feat[warp]);
+    emit((int)r, sm.feat[warp]);
+  }
+  __syncthreads();
   for (int r = blockIdx.x; r < n_rows; r += gridDim.x) {
     int64_t lo, hi;
     clamp_row(row_ptr, r, nnz, lo, hi);
-    row_features(w, lo, hi, k, sm, feat);
-    if (threadIdx.x < F) feats[(int64_t)r * F + threadIdx.x] = feat[threadIdx.x];
+    if (hi - lo <= WARP_ROW_MAX) continue;  // uniform over the block
+    block_row_features(w, lo, hi, k, sm, sm.feat[0]);
+    if (warp == 0) emit(r, sm.feat[0]);
+    __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(NT) features_kernel(const int64_t* row_ptr, const double* w, int n_rows,
+                                                      int64_t nnz, int k, float* feats) {
+  __shared__ FeatSmem sm;
+  for_each_row_features(row_ptr, w, n_rows, nnz, k, sm, [&](int r, const float* feat) {
+    const int lane = threadIdx.x & 31;
+    if (lane < F) feats[(int64_t)r * F + lane] = feat[lane];
+  });
 }
 
 // Row features, then the network on them, then the row's first-pass bound
@@ -281,27 +416,23 @@ __global__ void __launch_bounds__(NT) learned_bound_kernel(const int64_t* row_pt
                                                            float* t_row) {
   extern __shared__ __align__(16) float sp[];
   __shared__ FeatSmem sm;
-  __shared__ float feat[F];
-  __shared__ float h1[H];
+  __shared__ float h1[NW][H];
   load_params(params, sp);
-  for (int r = blockIdx.x; r < n_rows; r += gridDim.x) {
-    int64_t lo, hi;
-    clamp_row(row_ptr, r, nnz, lo, hi);
-    row_features(w, lo, hi, k, sm, feat);  // begins and ends with a block barrier
-    if (threadIdx.x < 32) {
-      float x[F];
+  __syncthreads();
+  for_each_row_features(row_ptr, w, n_rows, nnz, k, sm, [&](int r, const float* feat) {
+    float x[F];
 #pragma unroll
-      for (int f = 0; f < F; ++f) x[f] = feat[f];
-      Act A;
-      warp_forward(sp, x, h1, A);
-      if (threadIdx.x == 0) {
-        float T = expf(A.out - x[1] + margin);
-        if (!(T >= 1.0e-37f)) T = 1.0e-37f;  // tiny or NaN: the first pass fails, later passes are closed-form
-        if (!(T < 3.0e38f)) T = __int_as_float(0x7F800000);
-        t_row[r] = T;
-      }
+    for (int f = 0; f < F; ++f) x[f] = feat[f];
+    Act A;
+    warp_forward(sp, x, h1[threadIdx.x >> 5], A);
+    if ((threadIdx.x & 31) == 0) {
+      float T = expf(A.out - x[1] + margin);
+      if (!(T >= 1.0e-37f)) T = 1.0e-37f;  // tiny or NaN: the first pass fails, later passes are closed-form
+      if (!(T < 3.0e38f)) T = __int_as_float(0x7F800000);
+      t_row[r] = T;
     }
-  }
+    __syncwarp();
+  });
 }
 
 // ln of each row's largest register (+inf if a register is unfilled).

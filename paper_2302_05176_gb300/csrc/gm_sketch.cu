@@ -35,6 +35,7 @@
 #include <cstdio>
 #include <map>
 #include <mutex>
+#include <set>
 #include <utility>
 #include <vector>
 
@@ -45,9 +46,22 @@
 
 namespace gm {
 
-constexpr int BLOCK = 512;
+// Compile-time shape of the FastGM kernel (build-time overridable for experiments):
+// threads per CTA (CTAs per SM = 1024 / BLOCK), light-lane map capacity, lanes per
+// medium segment and its hash table.
+#ifndef GM_BLOCK
+#define GM_BLOCK 512
+#endif
+#ifndef GM_MAPCAP
+#define GM_MAPCAP 16
+#endif
+#ifndef GM_MED_SW
+#define GM_MED_SW 8
+#endif
+constexpr int BLOCK = GM_BLOCK;
 constexpr int WARPS = BLOCK / 32;
-constexpr int MAPCAP = 16;              // displaced positions a light lane can track
+constexpr int CTAS_PER_SM = 1024 / BLOCK;
+constexpr int MAPCAP = GM_MAPCAP;       // displaced positions a light lane can track
 // Default routing by the expected number of arrivals below T (gm_tuning): light
 // lanes up to LIGHT_MAX, 8-lane segments up to MEDIUM_MAX, 32-lane warps up to
 // HEAVY_MAX, dense permutations beyond; first-pass bound at quantile 1 - P_FIRST.
@@ -55,9 +69,9 @@ constexpr float LIGHT_MAX = 6.0f;
 constexpr float MEDIUM_MAX = 48.0f;
 constexpr float HEAVY_MAX = 256.0f;
 constexpr float P_FIRST = 0.05f;
-constexpr int MED_SW = 8;
-constexpr int MED_SLOTS = 128;          // hash slots per 8-lane segment
-constexpr int MED_MAX_FILL = 96;        // beyond: the element moves to a 32-lane warp
+constexpr int MED_SW = GM_MED_SW;
+constexpr int MED_SLOTS = 16 * MED_SW;  // hash slots per medium segment
+constexpr int MED_MAX_FILL = 12 * MED_SW;  // beyond: the element moves to a 32-lane warp
 constexpr uint32_t TAG_MEDIUM = 1u << 30, TAG_HEAVY = 2u << 30, TAG_SUPER = 3u << 30;
 constexpr uint32_t TAG_MASK = 3u << 30, SLOT_MASK = (1u << 30) - 1u;
 
@@ -224,6 +238,9 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
   int32_t id = 0;
   double R = 0.0;
   Fix acc = fix_zero();
+#ifdef GM_LIGHT_CONT
+  float tvu = 0.0f;  // T v (1 + 2^-20) of the lane's element, for the continuation screen
+#endif
   int wcount = 0;
   bool pool_done = false;
   while (true) {
@@ -270,7 +287,11 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
         e = (int)wbuf[wcount - 1 - rank];
         const int64_t g = lo + e;
         id = a.ids[g];
-        R = arr_rcp<ARITH>(a.w[g]);
+        const double v = a.w[g];
+        R = arr_rcp<ARITH>(v);
+#ifdef GM_LIGHT_CONT
+        tvu = (f32_trunc(v) * Tf) * (1.0f + 0x1p-20f);
+#endif
         z = 0;
         acc = fix_zero();
         msize = 0;
@@ -281,15 +302,27 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
     }
     if (!__any_sync(FULL, e >= 0)) break;  // nothing left to stream
     if (e < 0) continue;
-    const Words wd = philox((uint32_t)id, (uint32_t)z, a.key0, a.key1);
-    fix_add(acc, fix_from(arr_mul_t<ARITH>(arr_neglog<ARITH>(wd), __ldg(a.ctab + z))));
+    int J;
+#ifdef GM_LIGHT_CONT
+    {
+      const Words wd = philox((uint32_t)id, (uint32_t)z, a.key0, a.key1);
+      if (z > 0 && cont_screen_out(wd.w1, acc, tvu, k - z)) {  // certainly above T: the stream ends
+        ++cnt.screened;
+        e = -1;
+        continue;
+      }
+      J = randint(wd.w2, wd.w3, z, k);
+      fix_add(acc, fix_from(arr_mul_t<ARITH>(arr_neglog<ARITH>(wd), __ldg(a.ctab + z))));
+    }
+#else
+    fix_add(acc, arrival_term<ARITH>(id, z, k, a.key0, a.key1, a.ctab, J));
+#endif
     const uint64_t bb = (uint64_t)__double_as_longlong(arr_mul<ARITH>(fix_round(acc), R));
     ++cnt.arrivals;
     if (bb > Tbits) {  // FastPrune: the rest of this stream is above the bound
       e = -1;
       continue;
     }
-    const int J = randint(wd.w2, wd.w3, z, k);
     // Fisher-Yates step z on the sparse map (positions < z are final and dropped)
     int iz = -1;
     for (int i = 0; i < msize; ++i)
@@ -690,7 +723,7 @@ constexpr int MODE_MAIN = 0;
 constexpr int MODE_ESC = 1;
 
 template <int ARITH, int MODE>
-__global__ void __launch_bounds__(BLOCK, 2) fastgm_kernel(SketchArgs a) {
+__global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   SmemScalars& sh = sh_scalars;
   const int k = a.k;
@@ -989,7 +1022,7 @@ __global__ void __launch_bounds__(256) longprep_kernel(SketchArgs a) {
 
 // Dense permutations per CTA: as many as fit with two CTAs per SM (at least one).
 static int dense_buffers(int k, size_t smem_per_sm) {
-  const size_t budget = smem_per_sm / 2 - 2048;  // two CTAs, each with ~1 KB reserved and static smem
+  const size_t budget = smem_per_sm / CTAS_PER_SM - 2048;  // each CTA with ~1 KB reserved and static smem
   const size_t base = fast_smem_bytes(k, 0);
   if (budget <= base + pi_stride(k) * 2) return 1;
   const size_t n = (budget - base) / (pi_stride(k) * 2);
@@ -1001,10 +1034,32 @@ static double quantile_bound(double p, int k) {
   return -std::log(-std::expm1(std::log1p(-p) / (double)k));
 }
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
+// once per (kernel, device).  Calls on several host threads with different k
+// share the kernel: lowering the limit to one call's size could make another
+// call's launch fail, so the limit is only ever raised, and to the top.
+static int allow_max_smem(const void* kern) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GM_ECUDA;
+  std::lock_guard<std::mutex> g(mu);
+  if (done.count({kern, dev})) return GM_OK;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return GM_ECUDA;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return GM_ECUDA;
+  // the dynamic part may take what the kernel's static shared memory leaves
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes) !=
+      cudaSuccess)
+    return GM_ECUDA;
+  done.insert({kern, dev});
+  return GM_OK;
+}
+
 template <class KERNEL>
 static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
   int per_sm = 0;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return GM_ECUDA;
+  if (allow_max_smem((const void*)kern) != GM_OK) return GM_ECUDA;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, sm) != cudaSuccess) return GM_ECUDA;
   if (per_sm < 1) return GM_EINVAL;
   grid = nsm * per_sm;

@@ -116,6 +116,10 @@ def lib():
         L.gm_sketch_bounded.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                         ctypes.c_uint32, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
         L.gm_row_ystar.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
+        L.gm_sketch_host_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
+        L.gm_sketch_host_workspace_bytes.restype = ctypes.c_size_t
+        L.gm_sketch_host.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                     ctypes.c_uint32, _vp, _vp, _vp, ctypes.c_size_t]
         L.gm_strerror.argtypes = [ctypes.c_int]
         L.gm_strerror.restype = ctypes.c_char_p
         L.gm_version.restype = ctypes.c_char_p
@@ -495,3 +499,27 @@ def gm_row_ystar(y, out=None, stream=None):
     out = torch.empty(n, dtype=torch.float64, device=y.device) if out is None else out
     _check(lib().gm_row_ystar(_ptr(y), n, k, _ptr(out), _stream_handle(stream)), "gm_row_ystar")
     return out
+
+
+# --- host-memory batches (gm_sketch_host) --------------------------------------------------------
+
+def sketch_host_workspace(n_rows, nnz, k, device=None):
+    n = lib().gm_sketch_host_workspace_bytes(int(n_rows), int(nnz), int(k))
+    if n == 0:
+        raise GmError(GM_EINVAL, "gm_sketch_host_workspace_bytes")
+    return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
+
+
+def gm_sketch_host(row_ptr, ids, w, k, seed, flags=0, s_out=None, y_out=None, ws=None):
+    """gm_sketch over CPU tensors (pinned for asynchronous copies); returns CPU (s, y, ws)."""
+    for t, d, nm in ((row_ptr, torch.int64, "row_ptr"), (ids, torch.int32, "ids"), (w, torch.float64, "w")):
+        if t.is_cuda or t.dtype != d or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CPU %s tensor" % (nm, d))
+    n_rows, nnz = row_ptr.numel() - 1, ids.numel()
+    s_out = torch.empty((n_rows, k), dtype=torch.int32) if s_out is None else s_out
+    y_out = torch.empty((n_rows, k), dtype=torch.float64) if y_out is None else y_out
+    ws = sketch_host_workspace(n_rows, nnz, k) if ws is None else ws
+    _check(lib().gm_sketch_host(_ptr(row_ptr), _ptr(ids), _ptr(w), n_rows, nnz, int(k),
+                                int(seed) & 0xFFFFFFFFFFFFFFFF, int(flags), _ptr(s_out), _ptr(y_out), _ptr(ws),
+                                ws.numel()), "gm_sketch_host")
+    return s_out, y_out, ws
