@@ -1,10 +1,13 @@
 // gm_arith.cuh -- FP64 results computed on GB300's integer pipes.
 //
-// GB300 runs FP64 at about 1/64 of its FP32 rate (measured: 5.0e11 DFMA/s; a
+// GB300 runs FP64 at about 1/60 of its FP32 rate (measured: 6.3e11 DFMA/s; a
 // warp's FP64 instruction costs the same with one active lane as with 32), and
-// one FP64 log costs about 31 DFMA.  The arrival recurrence needs, per arrival,
-// one natural log and two products; here they are computed with 64/128-bit
-// integer arithmetic, which runs at 32-128 lane-ops per clock per SM:
+// CUDA's FP64 log runs at 1.75e10/s.  The arrival recurrence needs, per arrival,
+// one natural log and two products.  The logarithm below, in 64/128-bit integer
+// arithmetic, runs at 1.2e11/s and is what the sketch uses; the products and the
+// reciprocal are exact here too (bit-identical to the FP64 unit) and back the
+// all-integer arithmetic (GM_FLAG_INT_PRODUCTS), while the default sends those
+// to the otherwise idle FP64 unit:
 //
 //   neglog_u(w0, w1)  -ln(u) for u = (2m+1) 2^-53, m = top 52 bits of (w1:w0).
 //                     Tang's table-driven method (ACM TOMS 16(4), 1990) in fixed

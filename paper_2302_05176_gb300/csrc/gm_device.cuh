@@ -30,11 +30,7 @@ struct Words {
   uint32_t w0, w1, w2, w3;
 };
 
-#ifdef GM_NOINLINE_PHILOX
-static __device__ __noinline__ Words philox(uint32_t c0, uint32_t c1, uint32_t k0, uint32_t k1) {
-#else
 __device__ __forceinline__ Words philox(uint32_t c0, uint32_t c1, uint32_t k0, uint32_t k1) {
-#endif
   uint32_t c2 = 0u, c3 = 0u;
 #pragma unroll
   for (int round = 0; round < 10; ++round) {

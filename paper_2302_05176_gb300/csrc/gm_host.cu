@@ -9,6 +9,7 @@
 
 #include "gm.h"
 #include "gm_internal.h"
+#include "gm_trace.h"
 
 namespace gm {
 namespace host {
@@ -127,6 +128,7 @@ extern "C" int gm_sketch_host(const int64_t* row_ptr, const int32_t* ids, const 
   if (row_ptr[0] != 0 || row_ptr[n_rows] != nnz) return GM_EINVAL;
   for (int32_t r = 0; r < n_rows; ++r)
     if (row_ptr[r + 1] < row_ptr[r]) return GM_EINVAL;
+  const gm::TraceRange trace("gm_sketch_host");
   State& S = g_state;
   std::lock_guard<std::mutex> lock(S.mu);
   const int32_t rows = chunk_rows(n_rows);

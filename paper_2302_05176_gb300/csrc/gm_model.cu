@@ -20,6 +20,7 @@
 #include "gm.h"
 #include "gm_device.cuh"
 #include "gm_internal.h"
+#include "gm_trace.h"
 
 namespace gm {
 namespace mlp {
@@ -657,6 +658,7 @@ extern "C" int gm_model_grad(const float* params, const float* feats, const floa
   if (n < 1 || !params || !feats || !target || !grad || !loss || !workspace) return GM_EINVAL;
   if (!(tau > 0.0f && tau < 1.0f)) return GM_EINVAL;
   if (workspace_bytes < gm_model_grad_workspace_bytes()) return GM_ENOMEM;
+  const gm::TraceRange trace("gm_model_grad");
   if (cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRAD_SMEM) != cudaSuccess)
     return GM_ECUDA;
   float* part = static_cast<float*>(workspace);
@@ -721,6 +723,7 @@ extern "C" int gm_sketch_learned(const int64_t* row_ptr, const int32_t* ids, con
                                  size_t workspace_bytes, void* stream) {
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K || nnz > 0x7FFFFFFFll) return GM_EINVAL;
   if (!params || !std::isfinite(margin) || !workspace || !row_ptr) return GM_EINVAL;
+  const gm::TraceRange trace("gm_sketch_learned");
   const size_t base = gm_sketch_workspace_bytes(n_rows, nnz, k, 0u);
   const size_t need = gm_sketch_learned_workspace_bytes(n_rows, nnz, k);
   if (need == 0) return GM_EINVAL;

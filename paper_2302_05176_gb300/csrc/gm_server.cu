@@ -26,6 +26,7 @@
 #include "gm_estim.cuh"
 #include "gm_internal.h"
 #include "gm_server.h"
+#include "gm_trace.h"
 
 namespace gm {
 namespace srv {
@@ -409,6 +410,7 @@ static bool plan_sketch_batch(Server& S, SketchPlan& P) {
 // Copy the batch to the device and launch it (mutex NOT held: the requests are
 // RUNNING, so nothing else touches them or the slot).
 static int launch_sketch_batch(Server& S, SketchPlan& P, const std::vector<Req*>& rq) {
+  const TraceRange trace("gm_server sketch batch");
   Slot& sl = *P.slot;
   const int64_t m = (int64_t)rq.size();
   int64_t* rp_d = reinterpret_cast<int64_t*>(P.in);

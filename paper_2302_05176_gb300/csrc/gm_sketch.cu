@@ -43,6 +43,7 @@
 #include "gm_device.cuh"
 #include "gm_internal.h"
 #include "gm_stream.cuh"
+#include "gm_trace.h"
 
 namespace gm {
 
@@ -238,9 +239,6 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
   int32_t id = 0;
   double R = 0.0;
   Fix acc = fix_zero();
-#ifdef GM_LIGHT_CONT
-  float tvu = 0.0f;  // T v (1 + 2^-20) of the lane's element, for the continuation screen
-#endif
   int wcount = 0;
   bool pool_done = false;
   while (true) {
@@ -287,11 +285,7 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
         e = (int)wbuf[wcount - 1 - rank];
         const int64_t g = lo + e;
         id = a.ids[g];
-        const double v = a.w[g];
-        R = arr_rcp<ARITH>(v);
-#ifdef GM_LIGHT_CONT
-        tvu = (f32_trunc(v) * Tf) * (1.0f + 0x1p-20f);
-#endif
+        R = arr_rcp<ARITH>(a.w[g]);
         z = 0;
         acc = fix_zero();
         msize = 0;
@@ -303,20 +297,7 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
     if (!__any_sync(FULL, e >= 0)) break;  // nothing left to stream
     if (e < 0) continue;
     int J;
-#ifdef GM_LIGHT_CONT
-    {
-      const Words wd = philox((uint32_t)id, (uint32_t)z, a.key0, a.key1);
-      if (z > 0 && cont_screen_out(wd.w1, acc, tvu, k - z)) {  // certainly above T: the stream ends
-        ++cnt.screened;
-        e = -1;
-        continue;
-      }
-      J = randint(wd.w2, wd.w3, z, k);
-      fix_add(acc, fix_from(arr_mul_t<ARITH>(arr_neglog<ARITH>(wd), __ldg(a.ctab + z))));
-    }
-#else
     fix_add(acc, arrival_term<ARITH>(id, z, k, a.key0, a.key1, a.ctab, J));
-#endif
     const uint64_t bb = (uint64_t)__double_as_longlong(arr_mul<ARITH>(fix_round(acc), R));
     ++cnt.arrivals;
     if (bb > Tbits) {  // FastPrune: the rest of this stream is above the bound
@@ -407,9 +388,10 @@ __device__ __forceinline__ uint64_t refresh_bound(const Reg* regs, int k, uint64
   return t < Tbits ? t : Tbits;
 }
 
-// All warp-path classes of one pass, in order: 8-lane segments, 32-lane warps
-// (work list, then promotions), dense permutations (warps < ndense); the bound
-// is refreshed from y* before each class.
+// All warp-path classes of one pass: 8-lane segments, then without a barrier
+// the 32-lane warps' share of the work list (a warp's hash region is the same
+// in both), then the elements promoted out of 8-lane segments, then dense
+// permutations (warps < ndense); the bound is refreshed from y* at each barrier.
 template <int ARITH>
 __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uint64_t Tbits, Reg* regs,
                                             uint32_t* area, uint16_t* dense, SmemScalars& sh, Counters& cnt,
@@ -424,13 +406,18 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uin
                              a.plist + lo, &sh.pcount, cnt, gave_up);
   }
   clk_add(cnt, CLK_MEDIUM, t);
-  __syncthreads();
-  Tbits = refresh_bound(regs, a.k, Tbits, sh);
-  clk_add(cnt, CLK_WAIT, t);
+  // a warp's hash region is the same in both phases: the heavy list needs no barrier
   {
     const HashPi hp{area + warp * HASH_SLOTS};
     seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_heavy, TAG_HEAVY, hp, HASH_MAX_FILL, nullptr,
                          nullptr, cnt, gave_up);
+  }
+  clk_add(cnt, CLK_HEAVY, t);
+  __syncthreads();  // every promotion is listed
+  Tbits = refresh_bound(regs, a.k, Tbits, sh);
+  clk_add(cnt, CLK_WAIT, t);
+  {
+    const HashPi hp{area + warp * HASH_SLOTS};
     seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_pheavy, TAG_HEAVY, hp, HASH_MAX_FILL,
                          nullptr, nullptr, cnt, gave_up);
   }
@@ -1140,6 +1127,8 @@ static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const
                                void* workspace, size_t workspace_bytes, cudaStream_t stream, bool plain,
                                const float* t_row, const gm_tuning* tuning, const int32_t* init_s,
                                const double* init_y, const double* r_row) {
+  const TraceRange trace(plain ? (r_row ? "gm_sketch_budget" : "gm_sketch_plain")
+                               : (init_y ? "gm_stream_ingest" : (t_row ? "gm_sketch (per-row bounds)" : "gm_sketch")));
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K) return GM_EINVAL;
   if (init_y && (n_rows != 1 || plain)) return GM_EINVAL;
   if (nnz > 0x7FFFFFFFll) return GM_EINVAL;
@@ -1310,6 +1299,7 @@ extern "C" int gm_tune(const int64_t* row_ptr, const int32_t* ids, const double*
                        int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
                        size_t workspace_bytes, gm_tuning* best, double* best_ms, void* stream) {
   if (!best || k < 1 || k > GM_MAX_K || n_rows < 0 || nnz < 0) return GM_EINVAL;
+  const gm::TraceRange trace("gm_tune");
   const cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

@@ -68,31 +68,6 @@ __device__ __forceinline__ bool screen_out(uint32_t w1, float vf, float Tf, floa
   return w1 < thr_i;
 }
 
-// A lower bound of a prefix sum as FP32 (the high word, truncated; 0 below 2^-54).
-__device__ __forceinline__ float fix_to_f32_lower(const Fix& a) {
-  if (!a.w1) return 0.0f;
-  const int lead = 63 - __clzll((long long)a.w1);
-  const uint32_t mant = (uint32_t)((a.w1 << (63 - lead)) >> 40);  // 24 bits, leading one at bit 23
-  return __int_as_float(((lead - 54 + 127) << 23) | (int)(mant & 0x7FFFFFu));
-}
-
-// Continuation screen (light lanes, step z >= 1): with S = the exact sum before
-// step z and tvu >= T v (1 + 2^-21), arrival z is certainly above T when
-// E > (k - z) (T v (1 + 2^-48) - S), which the FP32 bound G below over-estimates;
-// b_z's roundings (log, two products, the sum, 1/v) cost less than 2^-48
-// relatively.  Then u < exp(-G) decides it as in screen_out.  False: not decided.
-__device__ __forceinline__ bool cont_screen_out(uint32_t w1, const Fix& S, float tvu, int m) {
-  if (!(tvu >= 1.17549435e-38f && tvu <= 1.0e30f)) return false;
-  const float sf = fix_to_f32_lower(S);
-  const float rem = (tvu - sf) + tvu * 0x1p-20f;  // >= T v (1 + 2^-48) - S, whatever the rounding
-  if (!(rem > 0.0f)) return false;
-  const float G = ((float)m * rem) * (1.0f + 0x1p-20f);
-  if (!(G <= 80.0f)) return false;  // exp(-G) below 2^-115: u can never be that small
-  const float thr = __expf(-G * (1.0f + 0x1p-18f)) * (1.0f - 0x1p-19f);
-  const uint32_t thr_i = (uint32_t)(thr * 4294967296.0f);
-  return w1 < thr_i;
-}
-
 // --------------------------------------------------------------------------
 // SW consecutive arrivals z0 .. z0+SW-1 of one element per SW-lane segment of the
 // warp (SW = 8 or 32), one per lane: returns the lane's arrival time (bits; all
@@ -102,12 +77,7 @@ __device__ __forceinline__ bool cont_screen_out(uint32_t w1, const Fix& S, float
 // --------------------------------------------------------------------------
 // One arrival's term t_z = RN(E C_z) as a fixed-point value and its RandInt target.
 template <int ARITH>
-#ifdef GM_NOINLINE_ARRIVAL
-static __device__ __noinline__
-#else
-__device__ __forceinline__
-#endif
-Fix arrival_term(int32_t id, int z, int k, uint32_t key0, uint32_t key1, const double* __restrict__ ctab, int& J) {
+__device__ __forceinline__ Fix arrival_term(int32_t id, int z, int k, uint32_t key0, uint32_t key1, const double* __restrict__ ctab, int& J) {
   const Words wd = philox((uint32_t)id, (uint32_t)z, key0, key1);
   J = randint(wd.w2, wd.w3, z, k);
   return fix_from(arr_mul_t<ARITH>(arr_neglog<ARITH>(wd), __ldg(ctab + z)));
@@ -180,8 +150,8 @@ template <int SLOTS>
 struct HashPiN {
   uint32_t* tab;
   static uint32_t* member_type();
-  static constexpr int BITS = SLOTS == 512 ? 9 : (SLOTS == 256 ? 8 : 7);
-  static_assert(SLOTS == 128 || SLOTS == 256 || SLOTS == 512, "hash size");
+  static constexpr int BITS = SLOTS == 512 ? 9 : (SLOTS == 256 ? 8 : (SLOTS == 128 ? 7 : 6));
+  static_assert(SLOTS == 64 || SLOTS == 128 || SLOTS == 256 || SLOTS == 512, "hash size");
   __device__ __forceinline__ static uint32_t slot(uint32_t p) { return (p * 0x9E3779B1u) >> (32 - BITS); }
   __device__ __forceinline__ uint32_t get(int p) const {
     uint32_t s = slot((uint32_t)p);
@@ -264,22 +234,7 @@ __device__ __forceinline__ int seg_fy_steps(const PI& pi, int z0, int J, int n, 
       src = s2;
     }
   }
-  const int key = act ? (int)(((uint32_t)base << 16) | (uint32_t)J) : -1 - lane;
-#ifdef GM_FY_SHFL_MATCH
-  // lanes of the segment holding the same target, by SW - 1 rotations (narrow segments)
-  uint32_t same = 1u << lane;
-  if constexpr (SW < 32) {
-#pragma unroll
-    for (int d = 1; d < SW; ++d) {
-      const int other = base + ((sl + d) & (SW - 1));
-      if (__shfl_sync(FULL, key, other) == key) same |= 1u << other;
-    }
-  } else {
-    same = __match_any_sync(FULL, key);
-  }
-#else
-  const uint32_t same = __match_any_sync(FULL, key);
-#endif
+  const uint32_t same = __match_any_sync(FULL, act ? (int)(((uint32_t)base << 16) | (uint32_t)J) : -1 - lane);
   const int pt = 31 - __clz(same & lt);
   const uint32_t a_pt = __shfl_sync(FULL, val, pt < 0 ? lane : pt);
   c_out = act ? (int)(pt >= 0 ? a_pt : pi.get(J)) : 0;
