@@ -146,7 +146,7 @@ LAUNCHES_PER_CALL = 5                           # init, plan, long-row prep, mai
 LEARNED_TAU = 0.95
 # DRAM bytes (read + write) of one main-kernel launch from ncu, valid only for the
 # kernel sources they were taken on (sha256 of csrc/, see kernel_source_sha).
-TRAFFIC = {"src_sha": None, "bytes": None}
+TRAFFIC = {"src_sha": "ec05a3140276615c", "bytes": 166886912 + 41027584}  # commit b4a9f3d, k=1024 batch
 
 
 MAIN_KERNEL_SOURCES = ("gm_sketch.cu", "gm_device.cuh", "gm_arith.cuh", "gm_stream.cuh", "gm_log_tables.h",
@@ -595,6 +595,17 @@ def serving_leg(args):
     bufs = {i: (torch.from_numpy(r.csr.ids).pin_memory(), torch.from_numpy(r.csr.w).pin_memory())
             for i, r in enumerate(reqs) if r.kind == "sketch"}  # a front end receives into page-locked memory
     gen_s = time.perf_counter() - t0
+    runs = [_serve_once(args, reqs, bufs) for _ in range(3)]
+    runs.sort(key=lambda r: r["p50_ms"])
+    out = dict(runs[1])  # the median run by p50 (the host is shared: single runs vary)
+    out["p50_ms_of_runs"] = [r["p50_ms"] for r in runs]
+    out["p99_ms_of_runs"] = [r["p99_ms"] for r in runs]
+    out["generate_s"] = gen_s
+    return out
+
+
+def _serve_once(args, reqs, bufs):
+    from paper_2302_05176_gb300 import server as S
     with S.Server(seed=SEED, device_bytes=16 << 30, n_streams=args.serve_streams, flags=args.serve_flags,
                   stage_pinned=args.serve_stage_pinned) as srv:
         rng = np.random.default_rng(7)
@@ -645,8 +656,7 @@ def serving_leg(args):
             "mean_batch_rows": float(np.mean(batch)), "arena_peak_bytes": st["arena_peak_bytes"],
             "staged_requests": st["staged_requests"], "direct_requests": st["direct_requests"],
             "scheduler_pack_ms": st["pack_ns"] / 1e6, "scheduler_launch_ms": st["launch_ns"] / 1e6,
-            "input": "pinned host buffers, copied by the engine inside the measured latency",
-            "generate_s": gen_s}
+            "input": "pinned host buffers, copied by the engine inside the measured latency"}
 
 
 def learned_ablation(args, timed, sketch_call, dev_csr, s_main, y_main, ms_main, st_main, n_rows):
