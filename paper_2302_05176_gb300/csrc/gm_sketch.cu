@@ -117,7 +117,6 @@ struct SmemScalars {
   int pool, hcount, pcount, c_med, c_heavy, c_pheavy, c_super, c_psuper, unit, last;
   float red_f[WARPS];
   int red_i[WARPS];
-  unsigned long long red_u[WARPS];
   double red_d[WARPS];
   unsigned long long clk[WARPS][NCLK];  // light, 8-lane, 32-lane, dense, barrier wait, setup, finish, total
 };
@@ -363,42 +362,17 @@ __device__ __forceinline__ void clk_add(Counters&, int which, long long& t) {
   t = now;
 }
 
-// FastPrune's bound, refreshed lazily (Sec. 2.2): once every register is filled,
-// the largest register y* bounds every arrival that can still lower a register,
-// so min(T, y*) replaces T.  Registers only decrease, so a y* read at a phase
-// boundary stays valid for the rest of the pass.  Block-wide (two barriers).
-__device__ __forceinline__ uint64_t refresh_bound(const Reg* regs, int k, uint64_t Tbits, SmemScalars& sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long m = 0ull;
-  for (int j = threadIdx.x; j < k; j += BLOCK) {
-    const unsigned long long y = regs[j].y;  // an unfilled register is +inf, above every bound
-    m = y > m ? y : m;
-  }
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    const unsigned long long o = __shfl_xor_sync(FULL, m, d);
-    m = o > m ? o : m;
-  }
-  if (lane == 0) sh.red_u[warp] = m;
-  __syncthreads();
-  unsigned long long t = 0ull;
-#pragma unroll
-  for (int q = 0; q < WARPS; ++q) t = sh.red_u[q] > t ? sh.red_u[q] : t;
-  __syncthreads();
-  return t < Tbits ? t : Tbits;
-}
-
 // All warp-path classes of one pass: 8-lane segments, then without a barrier
 // the 32-lane warps' share of the work list (a warp's hash region is the same
 // in both), then the elements promoted out of 8-lane segments, then dense
-// permutations (warps < ndense); the bound is refreshed from y* at each barrier.
+// permutations (warps < ndense).  (Lowering T to the running y* at the barriers
+// saved 2 % of the arrivals and cost more in barriers: measured and dropped.)
 template <int ARITH>
 __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uint64_t Tbits, Reg* regs,
                                             uint32_t* area, uint16_t* dense, SmemScalars& sh, Counters& cnt,
                                             bool& gave_up, long long& t) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nh = sh.hcount;
-  Tbits = refresh_bound(regs, a.k, Tbits, sh);
   {
     const int seg = lane / MED_SW;
     const HashPiN<MED_SLOTS> hp{area + (warp * (32 / MED_SW) + seg) * MED_SLOTS};
@@ -414,7 +388,6 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uin
   }
   clk_add(cnt, CLK_HEAVY, t);
   __syncthreads();  // every promotion is listed
-  Tbits = refresh_bound(regs, a.k, Tbits, sh);
   clk_add(cnt, CLK_WAIT, t);
   {
     const HashPi hp{area + warp * HASH_SLOTS};
@@ -423,7 +396,6 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uin
   }
   clk_add(cnt, CLK_HEAVY, t);
   __syncthreads();
-  Tbits = refresh_bound(regs, a.k, Tbits, sh);
   clk_add(cnt, CLK_WAIT, t);
   // dense permutations: the CTA's own, then as many as fit in the (now idle) hash area
   const int ndense = min(WARPS, a.ndense + (int)(fast_area_bytes() / (pi_stride(a.k) * 2)));
