@@ -470,13 +470,15 @@ def main():
         "gpu_launches": LAUNCHES_PER_CALL * args.steps,
         "clocks": clk,
     }
-    line["graph"] = graph_leg(args, timed, sketch_call, ms_main, (rp, ids, w))
-    if not args.no_pareto:
+    single = world == 1  # with several ranks only the timed step and e2e run: the legs below are per-GPU studies
+    if single:
+        line["graph"] = graph_leg(args, timed, sketch_call, ms_main, (rp, ids, w))
+    if single and not args.no_pareto:
         line["pareto_k4096"] = pareto_leg(args)
-    if not args.no_learned:
+    if single and not args.no_learned:
         line["learned_k1024"] = learned_ablation(args, timed, sketch_call, (rp, ids, w), s_main, y_main, ms_main,
                                                  st_main, n_rows)
-    if not args.no_serve:
+    if single and not args.no_serve:
         line["serving"] = serving_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(X, K_MAIN, SEED, n_rows=args.cpu_rows)
