@@ -146,7 +146,7 @@ LAUNCHES_PER_CALL = 5                           # init, plan, long-row prep, mai
 LEARNED_TAU = 0.95
 # DRAM bytes (read + write) of one main-kernel launch from ncu, valid only for the
 # kernel sources they were taken on (sha256 of csrc/, see kernel_source_sha).
-TRAFFIC = {"src_sha": "ec05a3140276615c", "bytes": 166886912 + 41027584}  # commit b4a9f3d, k=1024 batch
+TRAFFIC = {"src_sha": "b643162b6a2d1e8a", "bytes": 166826496 + 40945920}  # commit f2ac260, k=1024 batch
 
 
 MAIN_KERNEL_SOURCES = ("gm_sketch.cu", "gm_device.cuh", "gm_arith.cuh", "gm_stream.cuh", "gm_log_tables.h",

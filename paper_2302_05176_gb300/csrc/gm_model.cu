@@ -15,6 +15,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "gm.h"
@@ -245,6 +248,38 @@ __device__ __forceinline__ long long quant_rank(int np, int qi) {
   return r < 1 ? 1 : r;
 }
 
+// The four quantile bins of a histogram by one warp (lane l owns bins
+// [32 l, 32 l + 32)); every lane returns them.  hist: shared or global.
+__device__ __forceinline__ void warp_quantiles(const int* hist, int np, int (&qbin)[4]) {
+  const int lane = threadIdx.x & 31;
+  constexpr int PER = NBINS / 32;
+  int own = 0;
+  for (int q = 0; q < PER; ++q) own += hist[PER * lane + q];
+  int incl = own;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += y;
+  }
+#pragma unroll
+  for (int qi = 0; qi < 4; ++qi) {
+    const long long r = quant_rank(np, qi);
+    int bin = 0, c = incl - own;
+    bool found = false;  // (bins are signed: found is a flag of its own)
+    if (np > 0 && c < r && incl >= r)
+      for (int q = 0; q < PER; ++q) {
+        c += hist[PER * lane + q];
+        if (c >= r) {
+          bin = BIN_MIN + PER * lane + q;
+          found = true;
+          break;
+        }
+      }
+    const uint32_t who = __ballot_sync(FULL, found);
+    qbin[qi] = who ? __shfl_sync(FULL, bin, __ffs(who) - 1) : 0;
+  }
+}
+
 // Features of row [lo, hi) by one warp (rows of up to WARP_ROW_MAX elements):
 // no block barrier.  hist: the warp's NBINS counters; feat: its 8 floats.
 constexpr int64_t WARP_ROW_MAX = 4096;
@@ -266,34 +301,8 @@ __device__ void warp_row_features(const double* __restrict__ w, int64_t lo, int6
     mxb = o > mxb ? o : mxb;
   }
   __syncwarp();
-  // lane l owns bins [32 l, 32 l + 32)
-  constexpr int PER = NBINS / 32;
-  int own = 0;
-  for (int q = 0; q < PER; ++q) own += hist[PER * lane + q];
-  int incl = own;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int y = __shfl_up_sync(FULL, incl, d);
-    if (lane >= d) incl += y;
-  }
   int qbin[4];
-#pragma unroll
-  for (int qi = 0; qi < 4; ++qi) {
-    const long long r = quant_rank(np, qi);
-    int bin = 0, c = incl - own;
-    bool found = false;  // (bins are signed: found is a flag of its own)
-    if (np > 0 && c < r && incl >= r)
-      for (int q = 0; q < PER; ++q) {
-        c += hist[PER * lane + q];
-        if (c >= r) {
-          bin = BIN_MIN + PER * lane + q;
-          found = true;
-          break;
-        }
-      }
-    const uint32_t who = __ballot_sync(FULL, found);
-    qbin[qi] = who ? __shfl_sync(FULL, bin, __ffs(who) - 1) : 0;
-  }
+  warp_quantiles(hist, np, qbin);
   if (lane == 0) write_features(np, sum, mxb, qbin, k, feat);
   __syncwarp();
 }
@@ -410,30 +419,207 @@ __global__ void __launch_bounds__(NT) features_kernel(const int64_t* row_ptr, co
   });
 }
 
-// Row features, then the network on them, then the row's first-pass bound
+// ---------------------------------------------------------------------------
+// The learned bound of a batch.  Rows of up to WARP_ROW_MAX elements are done by
+// one warp each (features, network, bound: learned_short_kernel).  Longer rows
+// are listed and cut into PIECE-element pieces that the whole grid accumulates
+// (learned_piece_kernel: per-piece counts, sums and maxima, histograms added with
+// integer atomics); then one warp per long row adds its pieces in order and
+// finishes it (learned_long_kernel).  The result is the same bits every run.
+// ---------------------------------------------------------------------------
+constexpr int64_t PIECE = 8192;
+
+struct LongHdr {
+  unsigned long long n_long, n_pieces;  // 64-bit: no wrap even for overlapping (invalid) rows
+};
+struct LongEnt {
+  int row, piece_off, n_pieces, pad;
+};
+struct PiecePart {
+  int np, pad;
+  double sum;
+  unsigned long long mxb;
+};
+struct LearnedWs {
+  LongHdr* hdr;
+  LongEnt* longs;
+  int* piece_row;
+  int* hist;  // NBINS per long row
+  PiecePart* parts;
+  long long max_long, max_pieces;  // capacities (never reached by valid row offsets)
+};
+
+static int64_t learned_max_long(int64_t nnz) { return nnz / (WARP_ROW_MAX + 1) + 1; }
+static int64_t learned_max_pieces(int64_t nnz) { return nnz / PIECE + learned_max_long(nnz); }
+static size_t learned_ws_bytes(int64_t nnz) {
+  const int64_t ml = learned_max_long(nnz), mp = learned_max_pieces(nnz);
+  return 256 + round_up((size_t)ml * sizeof(LongEnt), 256) + round_up((size_t)mp * 4, 256) +
+         round_up((size_t)ml * NBINS * 4, 256) + round_up((size_t)mp * sizeof(PiecePart), 256);
+}
+static LearnedWs learned_ws(unsigned char* p, int64_t nnz) {
+  const int64_t ml = learned_max_long(nnz), mp = learned_max_pieces(nnz);
+  LearnedWs L;
+  L.hdr = reinterpret_cast<LongHdr*>(p);
+  p += 256;
+  L.longs = reinterpret_cast<LongEnt*>(p);
+  p += round_up((size_t)ml * sizeof(LongEnt), 256);
+  L.piece_row = reinterpret_cast<int*>(p);
+  p += round_up((size_t)mp * 4, 256);
+  L.hist = reinterpret_cast<int*>(p);
+  p += round_up((size_t)ml * NBINS * 4, 256);
+  L.parts = reinterpret_cast<PiecePart*>(p);
+  L.max_long = ml;
+  L.max_pieces = mp;
+  return L;
+}
+
+// The network on a warp's features, then the row's first-pass bound
 // T = exp(ln y* prediction + margin), made a positive normal float (or +inf).
-__global__ void __launch_bounds__(NT) learned_bound_kernel(const int64_t* row_ptr, const double* w, int n_rows,
+__device__ __forceinline__ void warp_emit_bound(const float* sp, const float* feat, float* h1w, float margin,
+                                                float* t_row, int r) {
+  float x[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) x[f] = feat[f];
+  Act A;
+  warp_forward(sp, x, h1w, A);
+  if ((threadIdx.x & 31) == 0) {
+    float T = expf(A.out - x[1] + margin);
+    if (!(T >= 1.0e-37f)) T = 1.0e-37f;  // tiny or NaN: the first pass fails, later passes are closed-form
+    if (!(T < 3.0e38f)) T = __int_as_float(0x7F800000);
+    t_row[r] = T;
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(NT) learned_short_kernel(const int64_t* row_ptr, const double* w, int n_rows,
                                                            int64_t nnz, int k, const float* params, float margin,
-                                                           float* t_row) {
+                                                           float* t_row, LearnedWs L) {
   extern __shared__ __align__(16) float sp[];
   __shared__ FeatSmem sm;
   __shared__ float h1[NW][H];
   load_params(params, sp);
   __syncthreads();
-  for_each_row_features(row_ptr, w, n_rows, nnz, k, sm, [&](int r, const float* feat) {
-    float x[F];
-#pragma unroll
-    for (int f = 0; f < F; ++f) x[f] = feat[f];
-    Act A;
-    warp_forward(sp, x, h1[threadIdx.x >> 5], A);
-    if ((threadIdx.x & 31) == 0) {
-      float T = expf(A.out - x[1] + margin);
-      if (!(T >= 1.0e-37f)) T = 1.0e-37f;  // tiny or NaN: the first pass fails, later passes are closed-form
-      if (!(T < 3.0e38f)) T = __int_as_float(0x7F800000);
-      t_row[r] = T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * NW + warp, nw = (int64_t)gridDim.x * NW;
+  for (int64_t r = gw; r < n_rows; r += nw) {
+    int64_t lo, hi;
+    clamp_row(row_ptr, (int)r, nnz, lo, hi);
+    if (hi - lo <= WARP_ROW_MAX) {
+      warp_row_features(w, lo, hi, k, sm.hist[warp], sm.feat[warp]);
+      warp_emit_bound(sp, sm.feat[warp], h1[warp], margin, t_row, (int)r);
+      continue;
     }
+    // a long row: list it, with its range of pieces, and clear its histogram.
+    // Rows that overlap (row offsets not ascending) can overrun the lists: such
+    // a row gets no learned bound (a negative T: the closed form).
+    const long long np = (hi - lo + PIECE - 1) / PIECE;
+    long long i = 0, off = 0;
+    if (lane == 0) {
+      i = (long long)atomicAdd(&L.hdr->n_long, 1ull);
+      off = (long long)atomicAdd(&L.hdr->n_pieces, (unsigned long long)np);
+    }
+    i = __shfl_sync(FULL, i, 0);
+    off = __shfl_sync(FULL, off, 0);
+    const bool ok = i < L.max_long && off + np <= L.max_pieces;
+    if (lane == 0) {
+      if (i < L.max_long) L.longs[i] = LongEnt{ok ? (int)r : -1, (int)off, (int)np, 0};
+      if (!ok) t_row[r] = -1.0f;
+    }
+    const long long pend = min(off + np, L.max_pieces);
+    for (long long g = off + lane; g < pend; g += 32) L.piece_row[g] = ok ? (int)i : -1;
+    if (ok)
+      for (int b = lane; b < NBINS; b += 32) L.hist[i * NBINS + b] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(NT) learned_piece_kernel(const int64_t* row_ptr, const double* w, int64_t nnz,
+                                                           LearnedWs L) {
+  __shared__ int hist[NW][NBINS];
+  __shared__ int red_i[NW];
+  __shared__ double red_s[NW];
+  __shared__ unsigned long long red_m[NW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long n_pieces = min((long long)L.hdr->n_pieces, L.max_pieces);
+  for (long long g = blockIdx.x; g < n_pieces; g += gridDim.x) {
+    const int i = L.piece_row[g];
+    if (i < 0) continue;  // uniform over the block
+    const LongEnt e = L.longs[i];
+    int64_t lo, hi;
+    clamp_row(row_ptr, e.row, nnz, lo, hi);
+    const int64_t plo = lo + (g - e.piece_off) * PIECE;
+    const int64_t phi = min(hi, plo + PIECE);
+    for (int b = tid; b < NW * NBINS; b += NT) (&hist[0][0])[b] = 0;
+    __syncthreads();
+    int np = 0;
+    ScaledSum acc{-1000000, 0.0f, 0.0f};
+    uint64_t mxb = 0ull;
+    feat_scan(w, plo + tid, phi, NT, hist[warp], np, acc, mxb);
+    double sum = ssum_value(acc);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      np += __shfl_xor_sync(FULL, np, d);
+      sum += __shfl_xor_sync(FULL, sum, d);
+      const uint64_t o = __shfl_xor_sync(FULL, mxb, d);
+      mxb = o > mxb ? o : mxb;
+    }
+    if (lane == 0) {
+      red_i[warp] = np;
+      red_s[warp] = sum;
+      red_m[warp] = mxb;
+    }
+    __syncthreads();
+    for (int b = tid; b < NBINS; b += NT) {
+      int c = 0;
+#pragma unroll
+      for (int w8 = 0; w8 < NW; ++w8) c += hist[w8][b];
+      if (c) atomicAdd(&L.hist[(int64_t)i * NBINS + b], c);
+    }
+    if (tid == 0) {
+      PiecePart pp;
+      pp.np = 0;
+      pp.pad = 0;
+      pp.sum = 0.0;
+      pp.mxb = 0ull;
+      for (int q = 0; q < NW; ++q) {
+        pp.np += red_i[q];
+        pp.sum += red_s[q];
+        pp.mxb = red_m[q] > pp.mxb ? red_m[q] : pp.mxb;
+      }
+      L.parts[g] = pp;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(NT) learned_long_kernel(int k, const float* params, float margin, float* t_row,
+                                                          LearnedWs L) {
+  extern __shared__ __align__(16) float sp[];
+  __shared__ float feat[NW][F];
+  __shared__ float h1[NW][H];
+  load_params(params, sp);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long n_long = min((long long)L.hdr->n_long, L.max_long);
+  for (long long i = (long long)blockIdx.x * NW + warp; i < n_long; i += (long long)gridDim.x * NW) {
+    const LongEnt e = L.longs[i];
+    if (e.row < 0) continue;  // uniform over the warp
+    int np = 0;
+    double sum = 0.0;
+    unsigned long long mxb = 0ull;
+    if (lane == 0)
+      for (int q = 0; q < e.n_pieces; ++q) {  // in piece order: the same sum every run
+        const PiecePart pp = L.parts[e.piece_off + q];
+        np += pp.np;
+        sum += pp.sum;
+        mxb = pp.mxb > mxb ? pp.mxb : mxb;
+      }
+    np = __shfl_sync(FULL, np, 0);
+    int qbin[4];
+    warp_quantiles(L.hist + i * NBINS, np, qbin);
+    if (lane == 0) write_features(np, sum, mxb, qbin, k, feat[warp]);
     __syncwarp();
-  });
+    warp_emit_bound(sp, feat[warp], h1[warp], margin, t_row, e.row);
+  }
 }
 
 // ln of each row's largest register (+inf if a register is unfilled).
@@ -608,6 +794,21 @@ using namespace gm::mlp;
 
 static int finish(cudaError_t e) { return e == cudaSuccess ? GM_OK : GM_ECUDA; }
 
+// Raise a kernel's dynamic shared memory limit to `bytes`, once per (kernel,
+// device): concurrent calls never see a half-set attribute.
+static int allow_smem(const void* kern, size_t bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GM_ECUDA;
+  std::lock_guard<std::mutex> g(mu);
+  if (done.count({kern, dev})) return GM_OK;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    return GM_ECUDA;
+  done.insert({kern, dev});
+  return GM_OK;
+}
+
 static int model_grid(int n_units, int per_sm) {
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
@@ -659,7 +860,7 @@ extern "C" int gm_model_grad(const float* params, const float* feats, const floa
   if (!(tau > 0.0f && tau < 1.0f)) return GM_EINVAL;
   if (workspace_bytes < gm_model_grad_workspace_bytes()) return GM_ENOMEM;
   const gm::TraceRange trace("gm_model_grad");
-  if (cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRAD_SMEM) != cudaSuccess)
+  if (allow_smem((const void*)grad_kernel, GRAD_SMEM) != GM_OK)
     return GM_ECUDA;
   float* part = static_cast<float*>(workspace);
   const cudaStream_t st = (cudaStream_t)stream;
@@ -714,7 +915,7 @@ extern "C" int gm_model_load(float* params, const char* path, void* stream) {
 extern "C" size_t gm_sketch_learned_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k) {
   const size_t base = gm_sketch_workspace_bytes(n_rows, nnz, k, 0u);
   if (base == 0) return 0;
-  return base + round_up((size_t)n_rows * 4, 256);
+  return base + round_up((size_t)n_rows * 4, 256) + learned_ws_bytes(nnz);
 }
 
 extern "C" int gm_sketch_learned(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
@@ -728,15 +929,20 @@ extern "C" int gm_sketch_learned(const int64_t* row_ptr, const int32_t* ids, con
   const size_t need = gm_sketch_learned_workspace_bytes(n_rows, nnz, k);
   if (need == 0) return GM_EINVAL;
   if (workspace_bytes < need) return GM_ENOMEM;
-  float* t_row = reinterpret_cast<float*>(static_cast<unsigned char*>(workspace) + base);
+  unsigned char* extra = static_cast<unsigned char*>(workspace) + base;
+  float* t_row = reinterpret_cast<float*>(extra);
+  const LearnedWs L = learned_ws(extra + round_up((size_t)n_rows * 4, 256), nnz);
   const cudaStream_t st = (cudaStream_t)stream;
   if (n_rows > 0 && nnz > 0 && w) {
-    if (cudaFuncSetAttribute(learned_bound_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PARAM_SMEM) !=
-        cudaSuccess)
-      return GM_ECUDA;
-    const int grid = model_grid(n_rows, 4);
+    const int grid = model_grid(1 << 30, 4);  // a full wave: the kernels stride over their work
     if (grid < 1) return GM_ECUDA;
-    learned_bound_kernel<<<grid, NT, PARAM_SMEM, st>>>(row_ptr, w, n_rows, nnz, k, params, margin, t_row);
+    if (allow_smem((const void*)learned_short_kernel, PARAM_SMEM) != GM_OK ||
+        allow_smem((const void*)learned_long_kernel, PARAM_SMEM) != GM_OK)
+      return GM_ECUDA;
+    if (cudaMemsetAsync(L.hdr, 0, sizeof(LongHdr), st) != cudaSuccess) return GM_ECUDA;
+    learned_short_kernel<<<grid, NT, PARAM_SMEM, st>>>(row_ptr, w, n_rows, nnz, k, params, margin, t_row, L);
+    learned_piece_kernel<<<grid, NT, 0, st>>>(row_ptr, w, nnz, L);
+    learned_long_kernel<<<grid, NT, PARAM_SMEM, st>>>(k, params, margin, t_row, L);
     if (cudaGetLastError() != cudaSuccess) return GM_ECUDA;
   }
   const uint32_t f = (flags & ~(uint32_t)GM_BOUND_MASK) | GM_BOUND_CLOSED;  // later passes: closed form

@@ -175,6 +175,35 @@ def test_learned_sketch_exact_for_any_model(k):
     assert rep["ok"], rep
 
 
+def test_learned_bound_of_every_row_length():
+    """Rows at the warp and piece limits (4,096 and 8,192 elements) and long rows
+    (their features gathered piece by piece over the grid) get the bound
+    exp(net(features) - ln sum v + margin) of their gm_features: the number of
+    rows whose learned pass falls back is the number predicted from gm_features,
+    the network and the sketch's own y*, at several margins."""
+    rng = np.random.default_rng(31)
+    lens = [4095, 4096, 4097, 8191, 8192, 8193, 16384, 16385, 24577, 100000, 250000]
+    lens += [int(n) for n in rng.integers(1, 60000, 29)]
+    rows = [(rng.choice(1 << 24, n, replace=False).astype(np.int32), rng.lognormal(0.0, 2.0, n)) for n in lens]
+    X = W.from_rows(rows)
+    rp, ids, w = gm.to_device(X)
+    k = 256
+    s0, y0, _ = gm.gm_sketch(rp, ids, w, k, 5)
+    params = gm.gm_model_init(3)
+    f = gm.gm_features(rp, ids, w, k)
+    pred = gm.gm_model_forward(params, f) - f[:, 1]
+    ystar = y0.max(dim=1).values
+    gaps = np.sort((torch.log(ystar) - pred.double()).cpu().numpy())
+    for q in (3, 20, 36):
+        margin = float(0.5 * (gaps[q] + gaps[q + 1]))  # between two rows: no decision sits on the edge
+        s, y, ws = gm.gm_sketch_learned(rp, ids, w, k, 5, params, margin)
+        code, st = gm.gm_status(ws)
+        assert code == gm.GM_OK
+        assert torch.equal(s, s0) and torch.equal(y.view(torch.int64), y0.view(torch.int64))
+        T = torch.exp(pred + margin)
+        assert st["rows_fallback"] == int((ystar > T.double()).sum()) == len(lens) - 1 - q, q
+
+
 def test_learned_sketch_arguments():
     X = edge_batch()
     rp, ids, w = gm.to_device(X)
