@@ -622,9 +622,9 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
       Td = f64_from_f32(Tf);
       for (int p = 1; p < pass; ++p) {  // passes >= 2 widen the bound by 16x each
         Td *= 16.0;
-        Tf = fminf(Tf * 16.0f, 3.0e38f);
+        Tf *= 16.0f;  // exact: the screen needs Tf = Td as reals, so no clamp below Td
       }
-      if (!(Td < 1.0e300)) last = true;
+      if (!(Td < 1.0e300) || !(Tf < 3.0e38f)) last = true;
     }
     const uint64_t Tbits = last ? DBL_MAX_BITS : (uint64_t)__double_as_longlong(Td);
     if (last) Tf = __int_as_float(0x7F800000);  // +inf: no screening, everything streams

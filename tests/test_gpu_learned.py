@@ -178,7 +178,7 @@ def test_learned_sketch_exact_for_any_model(k):
 def test_learned_bound_of_every_row_length():
     """Rows at the warp and piece limits (4,096 and 8,192 elements) and long rows
     (their features gathered piece by piece over the grid) get the bound
-    exp(net(features) - ln sum v + margin) of their gm_features: the number of
+    exp(gm_model_forward(gm_features) + margin): the number of
     rows whose learned pass falls back is the number predicted from gm_features,
     the network and the sketch's own y*, at several margins."""
     rng = np.random.default_rng(31)
@@ -191,7 +191,7 @@ def test_learned_bound_of_every_row_length():
     s0, y0, _ = gm.gm_sketch(rp, ids, w, k, 5)
     params = gm.gm_model_init(3)
     f = gm.gm_features(rp, ids, w, k)
-    pred = gm.gm_model_forward(params, f) - f[:, 1]
+    pred = gm.gm_model_forward(params, f)  # the predicted ln bound (the network's output - ln sum v)
     ystar = y0.max(dim=1).values
     gaps = np.sort((torch.log(ystar) - pred.double()).cpu().numpy())
     for q in (3, 20, 36):
