@@ -166,7 +166,7 @@ def kernel_source_sha():
 
 def alu_roofline(st, kernel_ms):
     """The main kernel against the integer/ALU issue roofline: algorithmic
-    lane-instructions (kept arrivals x 439.5 + screened elements x 88.1) per
+    lane-instructions (kept arrivals x 348.5 + screened elements x 88.1) per
     second of the kernel alone, over 152 SMs x 128 lanes x the maximum SM clock."""
     import torch
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
@@ -179,6 +179,46 @@ def alu_roofline(st, kernel_ms):
             "traffic": traffic, "kernel": "fastgm_kernel<2, 0>", "kernel_ms": kernel_ms,
             "peak_source": "derived: %d SMs x %d lanes x %.0f MHz" % (props.multi_processor_count, LANES_PER_SM, mhz),
             "work_lane_inst": work, "kept_arrivals": st["kept"], "screened_elements": st["elements"]}
+
+
+def fp64_pipe_view(kept, kernel_ms):
+    """The paper's arithmetic on the FP64 unit as a lower bound: every kept arrival
+    needs at least one FP64 -ln u and two FP64 products, so a design that computes
+    them there takes at least kept x (1 / log rate + 2 / product rate), the rates
+    measured here on the FP64 unit alone (include/gm_diag.h).  frac = that bound /
+    the main kernel's time (above 1: faster than any FP64-unit design could be)."""
+    import ctypes
+    import torch
+    from paper_2302_05176_gb300 import gm
+    L = gm.lib()
+    vp = ctypes.c_void_p
+    L.gm_diag_neglog.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
+    L.gm_diag_dmul.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
+    st = vp(torch.cuda.current_stream().cuda_stream)
+    P = lambda t: vp(t.data_ptr())
+    n = 1 << 23
+    rng = np.random.default_rng(0)
+    x = torch.from_numpy(rng.integers(0, 2**62, size=n, dtype=np.int64)).cuda()
+    a = torch.from_numpy(1.0 + rng.random(n)).cuda()
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    log_rate = n / (_time_ms(lambda: L.gm_diag_neglog(P(x), n, 1, P(y), st)) * 1e-3)
+    mul_rate = n / (_time_ms(lambda: L.gm_diag_dmul(P(a), P(a), n, 1, P(y), st)) * 1e-3)
+    t_min = kept * (1.0 / log_rate + 2.0 / mul_rate) * 1e3
+    return {"bound": "fp64 unit (paper's arithmetic)", "t_min_ms": t_min, "kernel_ms": kernel_ms,
+            "frac": t_min / kernel_ms, "neg_log_per_s": log_rate, "mul_per_s": mul_rate, "kept_arrivals": kept}
+
+
+def _time_ms(fn, reps=5):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 def max_sm_clock_mhz():
@@ -244,16 +284,7 @@ def run_arith(args):
     P = lambda t: vp(t.data_ptr())
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
 
-    def time_ms(fn, reps=5):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+    time_ms = _time_ms
 
     out = {"metric": "arithmetic throughput per GB300", "unit": "ops/s"}
     blocks, iters = nsm * 8, 4096
@@ -464,6 +495,7 @@ def main():
         "speedup_vs_plain_k1024": ms_plain / ms_main,
         "roofline": alu_roofline(st_main, kms_main),
         "hbm": hbm_figures(nnz, n_rows, K_MAIN, kms_main),
+        "fp64_view": fp64_pipe_view(st_main["kept"], kms_main),
         "e2e": {"value": world * n_rows / e2e_s, "unit": "sketches/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "tuning": tuned or "defaults",
