@@ -146,7 +146,7 @@ LAUNCHES_PER_CALL = 5                           # init, plan, long-row prep, mai
 LEARNED_TAU = 0.95
 # DRAM bytes (read + write) of one main-kernel launch from ncu, valid only for the
 # kernel sources they were taken on (sha256 of csrc/, see kernel_source_sha).
-TRAFFIC = {"src_sha": "b643162b6a2d1e8a", "bytes": 166826496 + 40945920}  # commit f2ac260, k=1024 batch
+TRAFFIC = {"src_sha": "8181c3d925ef6e9e", "bytes": 167330304 + 40821760}  # k=1024 batch
 
 
 MAIN_KERNEL_SOURCES = ("gm_sketch.cu", "gm_device.cuh", "gm_arith.cuh", "gm_stream.cuh", "gm_log_tables.h",
@@ -206,6 +206,51 @@ def fp64_pipe_view(kept, kernel_ms):
     t_min = kept * (1.0 / log_rate + 2.0 / mul_rate) * 1e3
     return {"bound": "fp64 unit (paper's arithmetic)", "t_min_ms": t_min, "kernel_ms": kernel_ms,
             "frac": t_min / kernel_ms, "neg_log_per_s": log_rate, "mul_per_s": mul_rate, "kept_arrivals": kept}
+
+
+def estimator_figures(s, y):
+    """The estimators and the union on the benchmark batch's sketches, each against
+    HBM with L2 flushed before every call: Jaccard of rows (i, i+1) reads 2 x 4k
+    bytes per pair, cardinality 8k per row, the union 2 x 12k in and 12k out per
+    row (8 bytes out per estimate)."""
+    import torch
+    from paper_2302_05176_gb300 import gm
+    n, k = s.shape
+    s_b, y_b = torch.roll(s, 1, 0).contiguous(), torch.roll(y, 1, 0).contiguous()
+    jo = torch.empty(n, dtype=torch.float64, device=s.device)
+    co = torch.empty(n, dtype=torch.float64, device=s.device)
+    ms_, my_ = torch.empty_like(s), torch.empty_like(y)
+    hbm_gbs, src = peaks()
+    out = {"hbm_peak_gbs": hbm_gbs, "hbm_peak_source": src}
+    for name, fn, nbytes in (("jaccard", lambda: gm.gm_jaccard(s, s_b, out=jo), n * (8 * k + 8)),
+                             ("cardinality", lambda: gm.gm_cardinality(y, out=co), n * (8 * k + 8)),
+                             ("merge", lambda: gm.gm_merge(s, y, s_b, y_b, s_out=ms_, y_out=my_), n * 36 * k)):
+        ms = _time_ms_cold(fn)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "algorithmic_bytes": nbytes, "gbs": gbs, "hbm_frac": gbs / hbm_gbs}
+    return out
+
+
+_FLUSH = []
+
+
+def _time_ms_cold(fn, reps=10):
+    """Mean device time of fn() with L2 flushed before each call (a 256 MB write
+    outside the timed events): for inputs smaller than the 129 MB L2."""
+    import torch
+    if not _FLUSH:
+        _FLUSH.append(torch.empty(256 << 20, dtype=torch.uint8, device="cuda"))
+    fn()
+    total = 0.0
+    for _ in range(reps):
+        _FLUSH[0].zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / reps
 
 
 def _time_ms(fn, reps=5):
@@ -460,7 +505,7 @@ def main():
     h_w = torch.from_numpy(X.w).pin_memory()
     h_s = torch.empty((n_rows, K_MAIN), dtype=torch.int32).pin_memory()
     h_y = torch.empty((n_rows, K_MAIN), dtype=torch.float64).pin_memory()
-    ws_host = gm.sketch_host_workspace(n_rows, nnz, K_MAIN)
+    ws_host = gm.sketch_host_workspace(n_rows, nnz, K_MAIN, row_ptr=h_rp)
 
     def e2e_step():  # gm_sketch_host: row chunks copied in, sketched, copied out on two streams
         gm.gm_sketch_host(h_rp, h_ids, h_w, K_MAIN, SEED, s_out=h_s, y_out=h_y, ws=ws_host)
@@ -496,6 +541,7 @@ def main():
         "roofline": alu_roofline(st_main, kms_main),
         "hbm": hbm_figures(nnz, n_rows, K_MAIN, kms_main),
         "fp64_view": fp64_pipe_view(st_main["kept"], kms_main),
+        "estimators": estimator_figures(s_main, y_main),
         "e2e": {"value": world * n_rows / e2e_s, "unit": "sketches/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "tuning": tuned or "defaults",
@@ -715,7 +761,16 @@ def learned_ablation(args, timed, sketch_call, dev_csr, s_main, y_main, ms_main,
     ms_n, kms_n, st_n, s_n, y_n = timed(sketch_call(gm.gm_sketch, K_MAIN, gm.GM_BOUND_NONE), K_MAIN,
                                         max(2, args.steps // 3), args.warmup)
     same = lambda s, y: bool(torch.equal(s, s_main) and torch.equal(y.view(torch.int64), y_main.view(torch.int64)))
+    # the pre-pass alone (features + network per row, gm_learned_bound): HBM-bound,
+    # algorithmic bytes = the weights and row offsets read once, the bounds written once
+    t_out = torch.empty(n_rows, dtype=torch.float32, device=rp.device)
+    lb_ws = torch.empty(gm.lib().gm_learned_bound_workspace_bytes(w.numel()), dtype=torch.uint8, device=rp.device)
+    pre_ms = _time_ms_cold(lambda: gm.gm_learned_bound(rp, w, K_MAIN, params, 0.0, out=t_out, ws=lb_ws))
+    pre_bytes = 8 * w.numel() + 8 * (n_rows + 1) + 4 * n_rows
+    hbm_gbs, hbm_src = peaks()
     return {
+        "prepass": {"ms": pre_ms, "algorithmic_bytes": pre_bytes, "gbs": pre_bytes / (pre_ms * 1e-3) / 1e9,
+                    "hbm_frac": pre_bytes / (pre_ms * 1e-3) / 1e9 / hbm_gbs, "hbm_peak_source": hbm_src},
         "train_sketches": int(ts.target.numel()), "train_set_s": t1 - t0, "train_s": t2 - t1,
         "train_steps": args.learned_steps, "tau": LEARNED_TAU, "final_pinball_loss": hist[-1][1],
         "sketches_per_s": n_rows / (ms_l * 1e-3), "ms_per_step": ms_l,

@@ -266,8 +266,24 @@ int gm_model_adam(float* params, float* adam, const float* grad, float lr, int32
 int gm_model_save(const float* params, const char* path, void* stream);
 int gm_model_load(float* params, const char* path, void* stream);
 
+/* The learned first-pass bound of every row of a CSR batch (device arrays):
+ * t_out[r] = exp(prediction_r + margin) as a positive FP32 value (clamped to
+ * [1e-37, +inf]), prediction_r = gm_model_forward of the row's gm_features.
+ * Rows of up to 4,096 elements take one warp each; longer rows are cut into
+ * 8,192-element pieces spread over the whole grid and combined in piece order,
+ * so t_out is the same bits on every call (the sum of a long row may differ
+ * from gm_features' in the last FP32 place).  A row with no positive weight
+ * gets the features of gm_features (zeros).  params: GM_MODEL_PARAMS floats;
+ * margin finite.  Workspace: gm_learned_bound_workspace_bytes(nnz) bytes of
+ * device memory.  Rows that overlap (row_ptr not ascending) may get t_out = -1
+ * (no learned bound) instead. */
+size_t gm_learned_bound_workspace_bytes(int64_t nnz);
+int gm_learned_bound(const int64_t* row_ptr, const double* w, int32_t n_rows, int64_t nnz, int32_t k,
+                     const float* params, float margin, float* t_out, void* workspace, size_t workspace_bytes,
+                     void* stream);
+
 /* gm_sketch with the first-pass bound of each row predicted by the model
- * (features and inference run on `stream` ahead of the sketch kernels):
+ * (gm_learned_bound, run on `stream` ahead of the sketch kernels):
  * T_r = exp(prediction_r + margin).  Same registers as gm_sketch.  Workspace:
  * gm_sketch_learned_workspace_bytes(). */
 size_t gm_sketch_learned_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k);
@@ -284,8 +300,9 @@ int gm_sketch_learned(const int64_t* row_ptr, const int32_t* ids, const double* 
  * a dense permutation beyond.  gm_sketch takes them from a process-wide table
  * keyed by (k, floor(log2(mean row length))), else the defaults (0.05, 6, 48,
  * 256).  gm_tune times candidate values on the caller's batch (coordinate
- * descent, each candidate the faster of two timed calls after one warm-up; it
- * synchronises `stream`), installs the fastest for that key and returns it.
+ * descent, up to two sweeps, each candidate the fastest of three timed calls
+ * after one warm-up and adopted when 1 % faster; it synchronises `stream`),
+ * installs the fastest for that key and returns it.
  * Requires 0 < p_first < 1 and 0 < light_max <= medium_max <= heavy_max. */
 typedef struct gm_tuning {
   float p_first;
@@ -351,15 +368,18 @@ int gm_stream_ingest(int32_t* s, double* y, int32_t k, const int32_t* ids, const
 /* ---- host-memory batches ---------------------------------------------------------
  * gm_sketch over a CSR batch in HOST memory (row_ptr, ids, w, s_out, y_out all
  * host arrays; page-locked ones are copied asynchronously, pageable ones through
- * the driver's staging).  The batch is cut into chunks of rows (at least 512,
- * about a quarter of the batch) that are copied to the device, sketched and
- * copied back on two streams, so the copies of one chunk overlap the sketch of
- * another.  Blocks until every register is in s_out / y_out.  The same registers
- * as gm_sketch on the whole batch.  row_ptr is checked on the host (GM_EINVAL:
- * row_ptr[0] != 0, decreasing, row_ptr[n_rows] != nnz).  workspace: device memory
- * of gm_sketch_host_workspace_bytes(n_rows, nnz, k) bytes.  Concurrent calls in
- * one process are serialised. */
+ * the CUDA runtime's staging buffers).  The batch is cut into chunks of rows (at
+ * least 128 rows, about a sixteenth of the batch) that are copied to the device,
+ * sketched and copied back on eight streams, so the copies of some chunks overlap
+ * the sketches of others.  Blocks until every register is in s_out / y_out.  The
+ * same registers as gm_sketch on the whole batch.  row_ptr is checked on the host
+ * (GM_EINVAL: row_ptr[0] != 0, decreasing, row_ptr[n_rows] != nnz).  workspace:
+ * device memory of gm_sketch_host_workspace_bytes_csr(row_ptr, n_rows, k) bytes
+ * (sized by the largest chunk; 0 for invalid row offsets), at most
+ * gm_sketch_host_workspace_bytes(n_rows, nnz, k) (any row offsets); GM_ENOMEM when
+ * smaller.  Concurrent calls in one process are serialised. */
 size_t gm_sketch_host_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k);
+size_t gm_sketch_host_workspace_bytes_csr(const int64_t* row_ptr, int32_t n_rows, int32_t k);
 int gm_sketch_host(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
                    int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
                    size_t workspace_bytes);

@@ -7,36 +7,47 @@
 
 namespace gm {
 
-constexpr int EST_BLOCK = 256;  // threads of a cardinality reduction (fixes its summation order)
+constexpr int EST_BLOCK = 256;  // threads per CTA of the estimator kernels (8 warps)
 
 // Fraction of registers where both sketches hold the same element (one warp).
+// 16-byte loads when both rows are 16-byte aligned and k % 4 == 0, four in
+// flight per lane; the count is an integer, so the path does not change it.
 __device__ __forceinline__ double warp_jaccard(const int32_t* __restrict__ a, const int32_t* __restrict__ b, int k) {
   const int lane = threadIdx.x & 31;
   int hits = 0;
-  for (int j = lane; j < k; j += 32) {
-    const int32_t x = a[j], y = b[j];
-    hits += (x >= 0 && x == y) ? 1 : 0;
+  if ((k & 3) == 0 && ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0) {
+    const int4* a4 = reinterpret_cast<const int4*>(a);
+    const int4* b4 = reinterpret_cast<const int4*>(b);
+    const int k4 = k >> 2;
+#pragma unroll 4
+    for (int j = lane; j < k4; j += 32) {
+      const int4 x = __ldg(a4 + j), y = __ldg(b4 + j);
+      hits += (x.x >= 0 && x.x == y.x) + (x.y >= 0 && x.y == y.y) + (x.z >= 0 && x.z == y.z) +
+              (x.w >= 0 && x.w == y.w);
+    }
+  } else {
+#pragma unroll 4
+    for (int j = lane; j < k; j += 32) {
+      const int32_t x = __ldg(a + j), y = __ldg(b + j);
+      hits += (x >= 0 && x == y) ? 1 : 0;
+    }
   }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) hits += __shfl_xor_sync(0xFFFFFFFFu, hits, d);
   return (double)hits / (double)k;
 }
 
-// (k - 1) / sum_j y_j by a block of EST_BLOCK threads: strided partial sums, a
-// butterfly per warp, then the warps in order.  part: EST_BLOCK / 32 shared
-// doubles.  The result is valid in thread 0; an unfilled register (+inf) gives 0.
-__device__ __forceinline__ double block_cardinality(const double* __restrict__ y, int k, double* part) {
+// (k - 1) / sum_j y_j by one warp: lane l adds y[l], y[l + 32], ... in order
+// (eight loads in flight), then a butterfly over the lanes; every lane returns
+// it.  An unfilled register (+inf) gives 0.
+__device__ __forceinline__ double warp_cardinality(const double* __restrict__ y, int k) {
+  const int lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int j = threadIdx.x; j < k; j += EST_BLOCK) s += y[j];
+#pragma unroll 8
+  for (int j = lane; j < k; j += 32) s += __ldg(y + j);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, d);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < EST_BLOCK / 32; ++q) t += part[q];
-  __syncthreads();
-  return (double)(k - 1) / t;
+  return (double)(k - 1) / s;
 }
 
 }  // namespace gm

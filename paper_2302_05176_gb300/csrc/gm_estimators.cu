@@ -17,13 +17,12 @@ __global__ void jaccard_kernel(const int32_t* __restrict__ sa, const int32_t* __
   }
 }
 
-// One CTA per row: FP64 tree sum of the registers, then (k - 1) / sum.
-__global__ void __launch_bounds__(EST_BLOCK) cardinality_kernel(const double* __restrict__ y, int n_rows, int k,
-                                                                double* __restrict__ out) {
-  __shared__ double part[EST_BLOCK / 32];
-  for (int r = blockIdx.x; r < n_rows; r += gridDim.x) {
-    const double c = block_cardinality(y + (int64_t)r * k, k, part);
-    if (threadIdx.x == 0) out[r] = c;
+// One warp per row: (k - 1) / sum of the registers.
+__global__ void cardinality_kernel(const double* __restrict__ y, int n_rows, int k, double* __restrict__ out) {
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); r < n_rows; r += warps) {
+    const double c = warp_cardinality(y + r * k, k);
+    if ((threadIdx.x & 31) == 0) out[r] = c;
   }
 }
 
@@ -66,7 +65,8 @@ extern "C" int gm_cardinality(const double* y, int32_t n_rows, int32_t k, double
   if (k < 2 || n_rows < 0) return GM_EINVAL;
   if (n_rows == 0) return GM_OK;
   if (!y || !out) return GM_EINVAL;
-  gm::cardinality_kernel<<<gm::grid_for(n_rows, 1), gm::EST_BLOCK, 0, (cudaStream_t)stream>>>(y, n_rows, k, out);
+  gm::cardinality_kernel<<<gm::grid_for(n_rows, gm::EST_BLOCK / 32), gm::EST_BLOCK, 0, (cudaStream_t)stream>>>(
+      y, n_rows, k, out);
   return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
 }
 

@@ -912,6 +912,38 @@ extern "C" int gm_model_load(float* params, const char* path, void* stream) {
   return finish(cudaStreamSynchronize(st));  // the host copy dies with this call
 }
 
+extern "C" size_t gm_learned_bound_workspace_bytes(int64_t nnz) {
+  return nnz < 0 ? 0 : learned_ws_bytes(nnz);
+}
+
+static int learned_bound_launch(const int64_t* row_ptr, const double* w, int32_t n_rows, int64_t nnz, int32_t k,
+                                const float* params, float margin, float* t_row, void* workspace,
+                                cudaStream_t st) {
+  if (n_rows == 0) return GM_OK;
+  const LearnedWs L = learned_ws(static_cast<unsigned char*>(workspace), nnz);
+  const int grid = model_grid(1 << 30, 4);  // a full wave: the kernels stride over their work
+  if (grid < 1) return GM_ECUDA;
+  if (allow_smem((const void*)learned_short_kernel, PARAM_SMEM) != GM_OK ||
+      allow_smem((const void*)learned_long_kernel, PARAM_SMEM) != GM_OK)
+    return GM_ECUDA;
+  if (cudaMemsetAsync(L.hdr, 0, sizeof(LongHdr), st) != cudaSuccess) return GM_ECUDA;
+  learned_short_kernel<<<grid, NT, PARAM_SMEM, st>>>(row_ptr, w, n_rows, nnz, k, params, margin, t_row, L);
+  learned_piece_kernel<<<grid, NT, 0, st>>>(row_ptr, w, nnz, L);
+  learned_long_kernel<<<grid, NT, PARAM_SMEM, st>>>(k, params, margin, t_row, L);
+  return finish(cudaGetLastError());
+}
+
+extern "C" int gm_learned_bound(const int64_t* row_ptr, const double* w, int32_t n_rows, int64_t nnz, int32_t k,
+                                const float* params, float margin, float* t_out, void* workspace,
+                                size_t workspace_bytes, void* stream) {
+  if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K || nnz > 0x7FFFFFFFll) return GM_EINVAL;
+  if (!params || !std::isfinite(margin) || !row_ptr || (n_rows > 0 && !t_out) || (nnz > 0 && !w) || !workspace)
+    return GM_EINVAL;
+  if (workspace_bytes < learned_ws_bytes(nnz)) return GM_ENOMEM;
+  const gm::TraceRange trace("gm_learned_bound");
+  return learned_bound_launch(row_ptr, w, n_rows, nnz, k, params, margin, t_out, workspace, (cudaStream_t)stream);
+}
+
 extern "C" size_t gm_sketch_learned_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k) {
   const size_t base = gm_sketch_workspace_bytes(n_rows, nnz, k, 0u);
   if (base == 0) return 0;
@@ -931,19 +963,11 @@ extern "C" int gm_sketch_learned(const int64_t* row_ptr, const int32_t* ids, con
   if (workspace_bytes < need) return GM_ENOMEM;
   unsigned char* extra = static_cast<unsigned char*>(workspace) + base;
   float* t_row = reinterpret_cast<float*>(extra);
-  const LearnedWs L = learned_ws(extra + round_up((size_t)n_rows * 4, 256), nnz);
   const cudaStream_t st = (cudaStream_t)stream;
   if (n_rows > 0 && nnz > 0 && w) {
-    const int grid = model_grid(1 << 30, 4);  // a full wave: the kernels stride over their work
-    if (grid < 1) return GM_ECUDA;
-    if (allow_smem((const void*)learned_short_kernel, PARAM_SMEM) != GM_OK ||
-        allow_smem((const void*)learned_long_kernel, PARAM_SMEM) != GM_OK)
-      return GM_ECUDA;
-    if (cudaMemsetAsync(L.hdr, 0, sizeof(LongHdr), st) != cudaSuccess) return GM_ECUDA;
-    learned_short_kernel<<<grid, NT, PARAM_SMEM, st>>>(row_ptr, w, n_rows, nnz, k, params, margin, t_row, L);
-    learned_piece_kernel<<<grid, NT, 0, st>>>(row_ptr, w, nnz, L);
-    learned_long_kernel<<<grid, NT, PARAM_SMEM, st>>>(k, params, margin, t_row, L);
-    if (cudaGetLastError() != cudaSuccess) return GM_ECUDA;
+    const int rc = learned_bound_launch(row_ptr, w, n_rows, nnz, k, params, margin, t_row,
+                                        extra + round_up((size_t)n_rows * 4, 256), st);
+    if (rc != GM_OK) return rc;
   }
   const uint32_t f = (flags & ~(uint32_t)GM_BOUND_MASK) | GM_BOUND_CLOSED;  // later passes: closed form
   return launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, f, s_out, y_out, workspace, base, st, false,

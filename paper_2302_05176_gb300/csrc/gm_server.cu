@@ -39,21 +39,13 @@ struct QDesc {
   int32_t kind;
 };
 
-// One CTA per query: Jaccard by its first warp, cardinality by the whole block
-// (the same reductions as gm_jaccard / gm_cardinality).
+// One warp per query (the same reductions as gm_jaccard / gm_cardinality).
 __global__ void __launch_bounds__(EST_BLOCK) query_kernel(const QDesc* __restrict__ q, int n, double* out) {
-  __shared__ double part[EST_BLOCK / 32];
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+  const int warps = gridDim.x * (EST_BLOCK / 32);
+  for (int i = blockIdx.x * (EST_BLOCK / 32) + (threadIdx.x >> 5); i < n; i += warps) {
     const QDesc d = q[i];
-    if (d.kind == GM_REQ_JACCARD) {
-      if (threadIdx.x < 32) {
-        const double j = warp_jaccard(d.sa, d.sb, d.k);
-        if (threadIdx.x == 0) out[i] = j;
-      }
-    } else {
-      const double c = block_cardinality(d.y, d.k, part);
-      if (threadIdx.x == 0) out[i] = c;
-    }
+    const double v = d.kind == GM_REQ_JACCARD ? warp_jaccard(d.sa, d.sb, d.k) : warp_cardinality(d.y, d.k);
+    if ((threadIdx.x & 31) == 0) out[i] = v;
   }
 }
 
@@ -546,7 +538,8 @@ static bool run_query_batch(Server& S) {
     if (cudaMemcpyAsync(qd, sl->h_q, (size_t)n * sizeof(QDesc), cudaMemcpyHostToDevice, st) != cudaSuccess)
       rc = GM_ECUDA;
     if (rc == GM_OK) {
-      query_kernel<<<std::min(n, 152 * 8), EST_BLOCK, 0, st>>>(qd, n, out);
+      query_kernel<<<std::min((n + EST_BLOCK / 32 - 1) / (EST_BLOCK / 32), 152 * 8), EST_BLOCK, 0, st>>>(qd, n,
+                                                                                                         out);
       if (cudaGetLastError() != cudaSuccess) rc = GM_ECUDA;
     }
     if (rc == GM_OK && cudaMemcpyAsync(sl->h_qout, out, (size_t)n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)

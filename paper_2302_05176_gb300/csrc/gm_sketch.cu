@@ -1283,7 +1283,7 @@ extern "C" int gm_tune(const int64_t* row_ptr, const int32_t* ids, const double*
                                      workspace_bytes, st, false, nullptr, &t);
     if (rc != GM_OK) return rc;
     float fastest = INFINITY;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
       if (cudaEventRecord(e0, st) != cudaSuccess) return GM_ECUDA;
       rc = gm::launch_sketch_tuned(row_ptr, ids, w, n_rows, nnz, k, seed, flags, s_out, y_out, workspace,
                                    workspace_bytes, st, false, nullptr, &t);
@@ -1309,18 +1309,25 @@ extern "C" int gm_tune(const int64_t* row_ptr, const int32_t* ids, const double*
     int n;
   } axes[] = {{&gm_tuning::p_first, p_cand, 6}, {&gm_tuning::light_max, l_cand, 5},
               {&gm_tuning::medium_max, m_cand, 5}, {&gm_tuning::heavy_max, h_cand, 4}};
-  for (const Axis& ax : axes) {
-    for (int i = 0; i < ax.n && rc == GM_OK; ++i) {
-      gm_tuning t = cur;
-      t.*(ax.field) = ax.vals[i];
-      if (t.*(ax.field) == cur.*(ax.field) || !gm::tuning_ok(t)) continue;
-      float ms = 0.0f;
-      rc = run(t, &ms);
-      if (rc == GM_OK && ms < 0.98f * t_cur) {
-        cur = t;
-        t_cur = ms;
+  // coordinate descent, at most two sweeps (the second only if the first moved);
+  // a candidate must beat the current choice by 1 %
+  for (int sweep = 0; sweep < 2 && rc == GM_OK; ++sweep) {
+    bool moved = false;
+    for (const Axis& ax : axes) {
+      for (int i = 0; i < ax.n && rc == GM_OK; ++i) {
+        gm_tuning t = cur;
+        t.*(ax.field) = ax.vals[i];
+        if (t.*(ax.field) == cur.*(ax.field) || !gm::tuning_ok(t)) continue;
+        float ms = 0.0f;
+        rc = run(t, &ms);
+        if (rc == GM_OK && ms < 0.99f * t_cur) {
+          cur = t;
+          t_cur = ms;
+          moved = true;
+        }
       }
     }
+    if (!moved) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

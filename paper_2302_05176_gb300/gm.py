@@ -87,6 +87,10 @@ def lib():
         L.gm_model_adam.argtypes = [_vp, _vp, _vp, ctypes.c_float, ctypes.c_int32, _vp]
         L.gm_model_save.argtypes = [_vp, ctypes.c_char_p, _vp]
         L.gm_model_load.argtypes = [_vp, ctypes.c_char_p, _vp]
+        L.gm_learned_bound_workspace_bytes.argtypes = [ctypes.c_int64]
+        L.gm_learned_bound_workspace_bytes.restype = ctypes.c_size_t
+        L.gm_learned_bound.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp, ctypes.c_float,
+                                       _vp, _vp, ctypes.c_size_t, _vp]
         L.gm_sketch_learned_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
         L.gm_sketch_learned_workspace_bytes.restype = ctypes.c_size_t
         L.gm_sketch_learned.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
@@ -118,6 +122,8 @@ def lib():
         L.gm_row_ystar.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
         L.gm_sketch_host_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
         L.gm_sketch_host_workspace_bytes.restype = ctypes.c_size_t
+        L.gm_sketch_host_workspace_bytes_csr.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
+        L.gm_sketch_host_workspace_bytes_csr.restype = ctypes.c_size_t
         L.gm_sketch_host.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                      ctypes.c_uint32, _vp, _vp, _vp, ctypes.c_size_t]
         L.gm_strerror.argtypes = [ctypes.c_int]
@@ -327,6 +333,21 @@ def gm_model_load(path, params=None, device=None, stream=None):
     return params
 
 
+def gm_learned_bound(row_ptr, w, k, params, margin=0.0, out=None, ws=None, stream=None):
+    """Per-row learned first-pass bound exp(prediction + margin), float32 [n_rows]."""
+    _need_cuda(row_ptr, torch.int64, "row_ptr")
+    _need_cuda(w, torch.float64, "w")
+    _need_cuda(params, torch.float32, "params")
+    n_rows, nnz = row_ptr.numel() - 1, w.numel()
+    dev = row_ptr.device
+    out = torch.empty(n_rows, dtype=torch.float32, device=dev) if out is None else out
+    if ws is None:
+        ws = torch.empty(max(1, lib().gm_learned_bound_workspace_bytes(nnz)), dtype=torch.uint8, device=dev)
+    _check(lib().gm_learned_bound(_ptr(row_ptr), _ptr(w), n_rows, nnz, int(k), _ptr(params), float(margin), _ptr(out),
+                                  _ptr(ws), ws.numel(), _stream_handle(stream)), "gm_learned_bound")
+    return out
+
+
 def sketch_learned_workspace_bytes(n_rows, nnz, k):
     n = lib().gm_sketch_learned_workspace_bytes(int(n_rows), int(nnz), int(k))
     if n == 0:
@@ -503,10 +524,20 @@ def gm_row_ystar(y, out=None, stream=None):
 
 # --- host-memory batches (gm_sketch_host) --------------------------------------------------------
 
-def sketch_host_workspace(n_rows, nnz, k, device=None):
-    n = lib().gm_sketch_host_workspace_bytes(int(n_rows), int(nnz), int(k))
+def sketch_host_workspace(n_rows, nnz, k, device=None, row_ptr=None):
+    """Device workspace for gm_sketch_host: sized by the batch's largest chunk when
+    the host row offsets are given, else for any row offsets."""
+    if row_ptr is not None:
+        rp = row_ptr
+        if not isinstance(rp, torch.Tensor) or rp.is_cuda or rp.dtype != torch.int64 or not rp.is_contiguous() or rp.numel() != int(n_rows) + 1:
+            raise ValueError("row_ptr must be a contiguous CPU int64 tensor of n_rows + 1 offsets")
+        n = lib().gm_sketch_host_workspace_bytes_csr(_ptr(rp), int(n_rows), int(k))
+        name = "gm_sketch_host_workspace_bytes_csr"
+    else:
+        n = lib().gm_sketch_host_workspace_bytes(int(n_rows), int(nnz), int(k))
+        name = "gm_sketch_host_workspace_bytes"
     if n == 0:
-        raise GmError(GM_EINVAL, "gm_sketch_host_workspace_bytes")
+        raise GmError(GM_EINVAL, name)
     return torch.empty(n, dtype=torch.uint8, device=device or torch.device("cuda"))
 
 
@@ -518,7 +549,7 @@ def gm_sketch_host(row_ptr, ids, w, k, seed, flags=0, s_out=None, y_out=None, ws
     n_rows, nnz = row_ptr.numel() - 1, ids.numel()
     s_out = torch.empty((n_rows, k), dtype=torch.int32) if s_out is None else s_out
     y_out = torch.empty((n_rows, k), dtype=torch.float64) if y_out is None else y_out
-    ws = sketch_host_workspace(n_rows, nnz, k) if ws is None else ws
+    ws = sketch_host_workspace(n_rows, nnz, k, row_ptr=row_ptr) if ws is None else ws
     _check(lib().gm_sketch_host(_ptr(row_ptr), _ptr(ids), _ptr(w), n_rows, nnz, int(k),
                                 int(seed) & 0xFFFFFFFFFFFFFFFF, int(flags), _ptr(s_out), _ptr(y_out), _ptr(ws),
                                 ws.numel()), "gm_sketch_host")

@@ -175,6 +175,35 @@ def test_learned_sketch_exact_for_any_model(k):
     assert rep["ok"], rep
 
 
+@pytest.mark.parametrize("k", [256, 4096])
+def test_learned_bound_against_features_and_oracle(k):
+    """gm_learned_bound: the same bits on every call; exp(gm_model_forward(gm_features)
+    + margin) to the FP32 rounding of the exponential for rows of up to 4,096
+    elements (the same feature code) and to that of a long row's sum beyond (its
+    pieces are added in piece order); and the FP64 oracle's features and network."""
+    rng = np.random.default_rng(41)
+    lens = [0, 1, 4095, 4096, 4097, 8191, 8192, 8193, 16385, 30000, 120000]
+    lens += [int(n) for n in rng.integers(1, 20000, 40)]
+    rows = [(rng.choice(1 << 24, n, replace=False).astype(np.int32), rng.lognormal(0.0, 1.5, n)) for n in lens]
+    rows[1] = (rows[1][0], np.array([0.0]))  # no positive weight
+    X = W.from_rows(rows)
+    rp, ids, w = gm.to_device(X)
+    theta = random_params(6).astype(np.float32)
+    params = to_dev(theta)
+    margin = 0.25
+    t1 = gm.gm_learned_bound(rp, w, k, params, margin)
+    t2 = gm.gm_learned_bound(rp, w, k, params, margin)
+    assert torch.equal(t1.view(torch.int32), t2.view(torch.int32))
+    f = gm.gm_features(rp, ids, w, k)
+    want = torch.exp(gm.gm_model_forward(params, f) + margin).cpu().numpy()
+    got = t1.cpu().numpy()
+    short = np.array([n <= 4096 for n in lens])
+    assert np.allclose(got[short], want[short], rtol=3e-7, atol=0), np.abs(got / want - 1)[short].max()
+    assert np.allclose(got[~short], want[~short], rtol=2e-5, atol=0), np.abs(got / want - 1)[~short].max()
+    pred, _ = mlp.forward(theta.astype(np.float64), mlp.features_rows(X.row_ptr, X.w, k))
+    assert np.allclose(got, np.exp(pred + margin), rtol=3e-4), np.abs(got / np.exp(pred + margin) - 1).max()
+
+
 def test_learned_bound_of_every_row_length():
     """Rows at the warp and piece limits (4,096 and 8,192 elements) and long rows
     (their features gathered piece by piece over the grid) get the bound

@@ -219,3 +219,19 @@ def test_lognormal_batch_full_size_sampled_rows():
     assert np.all(np.isfinite(y)) and np.all(y > 0)
     for r in rng.choice(X.n_rows, size=64, replace=False):
         assert np.isin(s[r], X.row(r)[0]).all()
+
+
+def test_pareto_heavy_full_size():
+    """16 rows x 10^6 elements, Pareto(1.2, x_min 1e-3), k = 4096, seed 1: the heavy-tail
+    launch the benchmark times.  FastGM equals the plain O(k n+) sketch on every
+    register of every row, and row 0 equals the oracle's Algorithm 1."""
+    X = W.pareto_heavy(seed=1)
+    k, seed = 4096, 1
+    rp, ids, w = gm.to_device(X)
+    s, y, _ = gm.gm_sketch(rp, ids, w, k, seed)
+    sp, yp, _ = gm.gm_sketch_plain(rp, ids, w, k, seed)
+    assert torch.equal(s, sp) and torch.equal(y.view(torch.int64), yp.view(torch.int64))
+    lo, hi = X.row_ptr[0], X.row_ptr[1]
+    s_ref, y_ref, _ = oracle.fastgm_alg1(X.ids[lo:hi], X.w[lo:hi], k, seed)
+    rep = compare_sketch(s[0].cpu().numpy(), y[0].cpu().numpy(), s_ref, y_ref)
+    assert rep["ok"], rep
