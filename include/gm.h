@@ -15,7 +15,9 @@
  *     device are recorded in the workspace and read back by gm_status().
  *   - The library allocates no memory.  Scratch space comes from a caller
  *     workspace whose size gm_sketch_workspace_bytes() reports.  Calls that
- *     share a workspace must be ordered (same stream, or synchronised).
+ *     share a workspace must be ordered (same stream, or synchronised).  A
+ *     workspace must start on a 256-byte boundary (as cudaMalloc returns; the
+ *     kernels use 16-byte atomics and loads inside it): GM_EINVAL otherwise.
  *   - All functions are thread-safe as long as concurrent calls use distinct
  *     workspaces.
  *
@@ -269,7 +271,7 @@ int gm_model_load(float* params, const char* path, void* stream);
 /* The learned first-pass bound of every row of a CSR batch (device arrays):
  * t_out[r] = exp(prediction_r + margin) as a positive FP32 value (clamped to
  * [1e-37, +inf]), prediction_r = gm_model_forward of the row's gm_features.
- * Rows of up to 4,096 elements take one warp each; longer rows are cut into
+ * Rows of up to 2,048 elements take one warp each; longer rows are cut into
  * 8,192-element pieces spread over the whole grid and combined in piece order,
  * so t_out is the same bits on every call (the sum of a long row may differ
  * from gm_features' in the last FP32 place).  A row with no positive weight

@@ -164,7 +164,9 @@ extern "C" int gm_sketch_host(const int64_t* row_ptr, const int32_t* ids, const 
                               int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out,
                               void* workspace, size_t workspace_bytes) {
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K || nnz > 0x7FFFFFFFll) return GM_EINVAL;
-  if (!row_ptr || !workspace || (n_rows > 0 && (!s_out || !y_out)) || (nnz > 0 && (!ids || !w))) return GM_EINVAL;
+  if (!row_ptr || !workspace || !gm::ws_aligned(workspace) || (n_rows > 0 && (!s_out || !y_out)) ||
+      (nnz > 0 && (!ids || !w)))
+    return GM_EINVAL;
   if (!rows_valid(row_ptr, n_rows, nnz)) return GM_EINVAL;
   const int32_t rows = chunk_rows(n_rows > 0 ? n_rows : 1);
   const int64_t cap = n_rows > 0 ? max_chunk_nnz(row_ptr, n_rows, rows) : 0;  // elements per slot

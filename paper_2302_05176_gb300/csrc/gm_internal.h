@@ -90,6 +90,10 @@ constexpr size_t ws_bytes(int32_t n_rows, int64_t nnz, int k) {
          round_up((size_t)max_long_rows(nnz) * (size_t)k * 16, 256) + round_up((size_t)max_long_rows(nnz) * 4, 256);
 }
 
+// Caller workspaces start on a 256-byte boundary (every region inside is laid
+// out at 256-byte offsets; 16-byte atomics and vector loads rely on it).
+inline bool ws_aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
 // The sketch launcher behind gm_sketch, gm_sketch_plain, gm_sketch_noalloc and
 // gm_sketch_learned.  t_row: per-row first-pass bounds (device floats) or null
 // for the closed-form bound.

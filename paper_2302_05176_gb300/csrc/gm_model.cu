@@ -203,10 +203,11 @@ struct FeatSmem {
 };
 
 // Accumulate elements [lo, hi) with stride `stride` from `first` into (np, sum,
-// max bits, histogram); four loads in flight per thread.
+// max bits, histogram); eight loads in flight per thread (a warp streaming a row
+// alone waits on HBM latency once per eight elements per lane).
 __device__ __forceinline__ void feat_scan(const double* __restrict__ w, int64_t first, int64_t hi, int stride,
                                           int* hist, int& np, ScaledSum& acc, uint64_t& mxb) {
-  constexpr int U = 4;
+  constexpr int U = 8;
   for (int64_t base = first; base < hi; base += (int64_t)U * stride) {
     double v[U];
 #pragma unroll
@@ -282,7 +283,7 @@ __device__ __forceinline__ void warp_quantiles(const int* hist, int np, int (&qb
 
 // Features of row [lo, hi) by one warp (rows of up to WARP_ROW_MAX elements):
 // no block barrier.  hist: the warp's NBINS counters; feat: its 8 floats.
-constexpr int64_t WARP_ROW_MAX = 4096;
+constexpr int64_t WARP_ROW_MAX = 2048;
 __device__ void warp_row_features(const double* __restrict__ w, int64_t lo, int64_t hi, int k, int* hist,
                                   float* feat) {
   const int lane = threadIdx.x & 31;
@@ -596,6 +597,7 @@ __global__ void __launch_bounds__(NT) learned_long_kernel(int k, const float* pa
   extern __shared__ __align__(16) float sp[];
   __shared__ float feat[NW][F];
   __shared__ float h1[NW][H];
+  __shared__ int hist[NW][NBINS];  // the row's histogram, staged for the quantile search
   load_params(params, sp);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -614,8 +616,12 @@ __global__ void __launch_bounds__(NT) learned_long_kernel(int k, const float* pa
         mxb = pp.mxb > mxb ? pp.mxb : mxb;
       }
     np = __shfl_sync(FULL, np, 0);
+    const int4* g4 = reinterpret_cast<const int4*>(L.hist + i * NBINS);
+    int4* s4 = reinterpret_cast<int4*>(hist[warp]);
+    for (int b = lane; b < NBINS / 4; b += 32) s4[b] = __ldcg(g4 + b);
+    __syncwarp();
     int qbin[4];
-    warp_quantiles(L.hist + i * NBINS, np, qbin);
+    warp_quantiles(hist[warp], np, qbin);
     if (lane == 0) write_features(np, sum, mxb, qbin, k, feat[warp]);
     __syncwarp();
     warp_emit_bound(sp, feat[warp], h1[warp], margin, t_row, e.row);
@@ -856,7 +862,7 @@ extern "C" size_t gm_model_grad_workspace_bytes(void) { return (size_t)GRAD_CTAS
 
 extern "C" int gm_model_grad(const float* params, const float* feats, const float* target, int32_t n, float tau,
                              float* grad, float* loss, void* workspace, size_t workspace_bytes, void* stream) {
-  if (n < 1 || !params || !feats || !target || !grad || !loss || !workspace) return GM_EINVAL;
+  if (n < 1 || !params || !feats || !target || !grad || !loss || !workspace || !ws_aligned(workspace)) return GM_EINVAL;
   if (!(tau > 0.0f && tau < 1.0f)) return GM_EINVAL;
   if (workspace_bytes < gm_model_grad_workspace_bytes()) return GM_ENOMEM;
   const gm::TraceRange trace("gm_model_grad");
@@ -937,7 +943,8 @@ extern "C" int gm_learned_bound(const int64_t* row_ptr, const double* w, int32_t
                                 const float* params, float margin, float* t_out, void* workspace,
                                 size_t workspace_bytes, void* stream) {
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K || nnz > 0x7FFFFFFFll) return GM_EINVAL;
-  if (!params || !std::isfinite(margin) || !row_ptr || (n_rows > 0 && !t_out) || (nnz > 0 && !w) || !workspace)
+  if (!params || !std::isfinite(margin) || !row_ptr || (n_rows > 0 && !t_out) || (nnz > 0 && !w) || !workspace ||
+      !ws_aligned(workspace))
     return GM_EINVAL;
   if (workspace_bytes < learned_ws_bytes(nnz)) return GM_ENOMEM;
   const gm::TraceRange trace("gm_learned_bound");
@@ -955,7 +962,7 @@ extern "C" int gm_sketch_learned(const int64_t* row_ptr, const int32_t* ids, con
                                  float margin, int32_t* s_out, double* y_out, void* workspace,
                                  size_t workspace_bytes, void* stream) {
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K || nnz > 0x7FFFFFFFll) return GM_EINVAL;
-  if (!params || !std::isfinite(margin) || !workspace || !row_ptr) return GM_EINVAL;
+  if (!params || !std::isfinite(margin) || !workspace || !ws_aligned(workspace) || !row_ptr) return GM_EINVAL;
   const gm::TraceRange trace("gm_sketch_learned");
   const size_t base = gm_sketch_workspace_bytes(n_rows, nnz, k, 0u);
   const size_t need = gm_sketch_learned_workspace_bytes(n_rows, nnz, k);

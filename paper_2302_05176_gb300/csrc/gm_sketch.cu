@@ -1104,7 +1104,8 @@ static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K) return GM_EINVAL;
   if (init_y && (n_rows != 1 || plain)) return GM_EINVAL;
   if (nnz > 0x7FFFFFFFll) return GM_EINVAL;
-  if (!workspace || !row_ptr || (n_rows > 0 && (!s_out || !y_out)) || (nnz > 0 && (!ids || !w)))
+  if (!workspace || !ws_aligned(workspace) || !row_ptr || (n_rows > 0 && (!s_out || !y_out)) ||
+      (nnz > 0 && (!ids || !w)))
     return GM_EINVAL;
   const uint32_t bound = flags & GM_BOUND_MASK;
   if (!plain && bound == GM_BOUND_LEARNED) return GM_EINVAL;  // needs a trained model
@@ -1396,7 +1397,8 @@ extern "C" int gm_stream_reset(int32_t* s, double* y, int32_t k, void* stream) {
 
 extern "C" int gm_stream_ingest(int32_t* s, double* y, int32_t k, const int32_t* ids, const double* w, int64_t n,
                                 uint64_t seed, uint32_t flags, void* workspace, size_t workspace_bytes, void* stream) {
-  if (!s || !y || k < 1 || k > GM_MAX_K || n < 0 || n > 0x7FFFFFFFll || (n > 0 && (!ids || !w)) || !workspace)
+  if (!s || !y || k < 1 || k > GM_MAX_K || n < 0 || n > 0x7FFFFFFFll || (n > 0 && (!ids || !w)) || !workspace ||
+      !gm::ws_aligned(workspace))
     return GM_EINVAL;
   if ((flags & GM_BOUND_MASK) == GM_BOUND_LEARNED) return GM_EINVAL;
   const size_t base = gm::ws_bytes(1, n, k);
@@ -1468,7 +1470,7 @@ extern "C" int gm_sketch_bounded(const int64_t* row_ptr, const int32_t* ids, con
                                  int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, const double* bound_row,
                                  int32_t* s_out, double* y_out, void* workspace, size_t workspace_bytes,
                                  void* stream) {
-  if (n_rows < 0 || (n_rows > 0 && !bound_row) || !workspace) return GM_EINVAL;
+  if (n_rows < 0 || (n_rows > 0 && !bound_row) || !workspace || !gm::ws_aligned(workspace)) return GM_EINVAL;
   if ((flags & GM_BOUND_MASK) == GM_BOUND_LEARNED) return GM_EINVAL;
   const size_t need = gm_sketch_bounded_workspace_bytes(n_rows, nnz, k);
   if (need == 0) return GM_EINVAL;

@@ -178,11 +178,11 @@ def test_learned_sketch_exact_for_any_model(k):
 @pytest.mark.parametrize("k", [256, 4096])
 def test_learned_bound_against_features_and_oracle(k):
     """gm_learned_bound: the same bits on every call; exp(gm_model_forward(gm_features)
-    + margin) to the FP32 rounding of the exponential for rows of up to 4,096
+    + margin) to the FP32 rounding of the exponential for rows of up to 2,048
     elements (the same feature code) and to that of a long row's sum beyond (its
     pieces are added in piece order); and the FP64 oracle's features and network."""
     rng = np.random.default_rng(41)
-    lens = [0, 1, 4095, 4096, 4097, 8191, 8192, 8193, 16385, 30000, 120000]
+    lens = [0, 1, 2047, 2048, 2049, 4096, 8191, 8192, 8193, 16385, 30000, 120000]
     lens += [int(n) for n in rng.integers(1, 20000, 40)]
     rows = [(rng.choice(1 << 24, n, replace=False).astype(np.int32), rng.lognormal(0.0, 1.5, n)) for n in lens]
     rows[1] = (rows[1][0], np.array([0.0]))  # no positive weight
@@ -197,7 +197,7 @@ def test_learned_bound_against_features_and_oracle(k):
     f = gm.gm_features(rp, ids, w, k)
     want = torch.exp(gm.gm_model_forward(params, f) + margin).cpu().numpy()
     got = t1.cpu().numpy()
-    short = np.array([n <= 4096 for n in lens])
+    short = np.array([n <= 2048 for n in lens])
     assert np.allclose(got[short], want[short], rtol=3e-7, atol=0), np.abs(got / want - 1)[short].max()
     assert np.allclose(got[~short], want[~short], rtol=2e-5, atol=0), np.abs(got / want - 1)[~short].max()
     pred, _ = mlp.forward(theta.astype(np.float64), mlp.features_rows(X.row_ptr, X.w, k))
@@ -205,13 +205,13 @@ def test_learned_bound_against_features_and_oracle(k):
 
 
 def test_learned_bound_of_every_row_length():
-    """Rows at the warp and piece limits (4,096 and 8,192 elements) and long rows
+    """Rows at the warp and piece limits (2,048 and 8,192 elements) and long rows
     (their features gathered piece by piece over the grid) get the bound
     exp(gm_model_forward(gm_features) + margin): the number of
     rows whose learned pass falls back is the number predicted from gm_features,
     the network and the sketch's own y*, at several margins."""
     rng = np.random.default_rng(31)
-    lens = [4095, 4096, 4097, 8191, 8192, 8193, 16384, 16385, 24577, 100000, 250000]
+    lens = [2047, 2048, 2049, 8191, 8192, 8193, 16384, 16385, 24577, 100000, 250000]
     lens += [int(n) for n in rng.integers(1, 60000, 29)]
     rows = [(rng.choice(1 << 24, n, replace=False).astype(np.int32), rng.lognormal(0.0, 2.0, n)) for n in lens]
     X = W.from_rows(rows)

@@ -161,6 +161,13 @@ def test_host_errors():
     tiny = torch.empty(8, dtype=torch.uint8, device="cuda")
     with pytest.raises(gm.GmError):
         gm.gm_sketch(rp, ids, w, 16, 1, ws=tiny)
+    # a workspace off the 256-byte boundary is refused before any launch
+    big = torch.empty(gm.lib().gm_sketch_workspace_bytes(1, X.nnz, 16, 0) + 256, dtype=torch.uint8, device="cuda")
+    for off in (16, 128):
+        with pytest.raises(gm.GmError) as e:
+            gm.gm_sketch(rp, ids, w, 16, 1, ws=big[off:])
+        assert e.value.code == gm.GM_EINVAL
+    gm.gm_sketch(rp, ids, w, 16, 1, ws=big[256:])
 
 
 def test_estimators_against_oracle():
