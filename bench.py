@@ -764,7 +764,8 @@ def learned_ablation(args, timed, sketch_call, dev_csr, s_main, y_main, ms_main,
     # the pre-pass alone (features + network per row, gm_learned_bound): HBM-bound,
     # algorithmic bytes = the weights and row offsets read once, the bounds written once
     t_out = torch.empty(n_rows, dtype=torch.float32, device=rp.device)
-    lb_ws = torch.empty(gm.lib().gm_learned_bound_workspace_bytes(w.numel()), dtype=torch.uint8, device=rp.device)
+    lb_ws = torch.empty(gm.lib().gm_learned_bound_workspace_bytes(n_rows, w.numel()), dtype=torch.uint8,
+                        device=rp.device)
     pre_ms = _time_ms_cold(lambda: gm.gm_learned_bound(rp, w, K_MAIN, params, 0.0, out=t_out, ws=lb_ws))
     pre_bytes = 8 * w.numel() + 8 * (n_rows + 1) + 4 * n_rows
     hbm_gbs, hbm_src = peaks()

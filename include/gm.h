@@ -272,14 +272,14 @@ int gm_model_load(float* params, const char* path, void* stream);
  * t_out[r] = exp(prediction_r + margin) as a positive FP32 value (clamped to
  * [1e-37, +inf]), prediction_r = gm_model_forward of the row's gm_features.
  * Rows of up to 2,048 elements take one warp each; longer rows are cut into
- * 8,192-element pieces spread over the whole grid and combined in piece order,
- * so t_out is the same bits on every call (the sum of a long row may differ
+ * 2,048-element pieces, one warp each over the whole grid, combined in a fixed
+ * order, so t_out is the same bits on every call (the sum of a long row may differ
  * from gm_features' in the last FP32 place).  A row with no positive weight
  * gets the features of gm_features (zeros).  params: GM_MODEL_PARAMS floats;
- * margin finite.  Workspace: gm_learned_bound_workspace_bytes(nnz) bytes of
- * device memory.  Rows that overlap (row_ptr not ascending) may get t_out = -1
+ * margin finite.  Workspace: gm_learned_bound_workspace_bytes(n_rows, nnz) bytes
+ * of device memory.  Rows that overlap (row_ptr not ascending) may get t_out = -1
  * (no learned bound) instead. */
-size_t gm_learned_bound_workspace_bytes(int64_t nnz);
+size_t gm_learned_bound_workspace_bytes(int32_t n_rows, int64_t nnz);
 int gm_learned_bound(const int64_t* row_ptr, const double* w, int32_t n_rows, int64_t nnz, int32_t k,
                      const float* params, float margin, float* t_out, void* workspace, size_t workspace_bytes,
                      void* stream);

@@ -228,20 +228,24 @@ __device__ __forceinline__ void feat_scan(const double* __restrict__ w, int64_t 
   }
 }
 
-// The eight features from (np, sum, max, quantile bins).
-__device__ __forceinline__ void write_features(int np, double sum, uint64_t mxb, const int* qbin, int k,
-                                               float* feat) {
-  if (np > 0) {
-    feat[0] = (float)log((double)np);
-    feat[1] = (float)log(sum);
-    feat[2] = (float)log(__longlong_as_double((long long)mxb));
-#pragma unroll
-    for (int qi = 0; qi < 4; ++qi) feat[3 + qi] = (float)(((double)qbin[qi] + 0.5) * (0.69314718055994531 / 4.0));
-  } else {
-#pragma unroll
-    for (int f = 0; f < 7; ++f) feat[f] = 0.0f;
+// The eight features from (np, sum, max, quantile bins), one per lane of a warp
+// (lanes 0 .. 7; every lane passes the same np, sum, mxb, qbin): the four FP64
+// logarithms run in one pass over the warp, as a warp's FP64 instruction costs
+// the same with one active lane as with four.
+__device__ __forceinline__ void warp_write_features(int np, double sum, uint64_t mxb, const int* qbin, int k,
+                                                    float* feat) {
+  const int lane = threadIdx.x & 31;
+  if (lane >= F) return;
+  float f = 0.0f;
+  if (lane >= 3 && lane < 7) {
+    const int qb = lane == 3 ? qbin[0] : (lane == 4 ? qbin[1] : (lane == 5 ? qbin[2] : qbin[3]));
+    if (np > 0) f = (float)(((double)qb + 0.5) * (0.69314718055994531 / 4.0));
+  } else if (np > 0 || lane == 7) {
+    const double x = lane == 0 ? (double)np
+                               : (lane == 1 ? sum : (lane == 2 ? __longlong_as_double((long long)mxb) : (double)k));
+    f = (float)log(x);
   }
-  feat[7] = (float)log((double)k);
+  feat[lane] = f;
 }
 
 __device__ __forceinline__ long long quant_rank(int np, int qi) {
@@ -284,16 +288,18 @@ __device__ __forceinline__ void warp_quantiles(const int* hist, int np, int (&qb
 // Features of row [lo, hi) by one warp (rows of up to WARP_ROW_MAX elements):
 // no block barrier.  hist: the warp's NBINS counters; feat: its 8 floats.
 constexpr int64_t WARP_ROW_MAX = 2048;
-__device__ void warp_row_features(const double* __restrict__ w, int64_t lo, int64_t hi, int k, int* hist,
-                                  float* feat) {
+// The statistics of row [lo, hi) by one warp: positive count, sum, max bits and
+// the four quantile bins (every lane returns them).  hist: the warp's NBINS counters.
+__device__ __forceinline__ void warp_row_stats(const double* __restrict__ w, int64_t lo, int64_t hi, int* hist,
+                                               int& np, double& sum, uint64_t& mxb, int (&qbin)[4]) {
   const int lane = threadIdx.x & 31;
   for (int b = lane; b < NBINS; b += 32) hist[b] = 0;
   __syncwarp();
-  int np = 0;
+  np = 0;
   ScaledSum acc{-1000000, 0.0f, 0.0f};
-  uint64_t mxb = 0ull;
+  mxb = 0ull;
   feat_scan(w, lo + lane, hi, 32, hist, np, acc, mxb);
-  double sum = ssum_value(acc);
+  sum = ssum_value(acc);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
     np += __shfl_xor_sync(FULL, np, d);
@@ -302,9 +308,16 @@ __device__ void warp_row_features(const double* __restrict__ w, int64_t lo, int6
     mxb = o > mxb ? o : mxb;
   }
   __syncwarp();
-  int qbin[4];
   warp_quantiles(hist, np, qbin);
-  if (lane == 0) write_features(np, sum, mxb, qbin, k, feat);
+}
+
+__device__ void warp_row_features(const double* __restrict__ w, int64_t lo, int64_t hi, int k, int* hist,
+                                  float* feat) {
+  int np, qbin[4];
+  double sum;
+  uint64_t mxb;
+  warp_row_stats(w, lo, hi, hist, np, sum, mxb, qbin);
+  warp_write_features(np, sum, mxb, qbin, k, feat);
   __syncwarp();
 }
 
@@ -373,7 +386,7 @@ __device__ void block_row_features(const double* __restrict__ w, int64_t lo, int
     }
   }
   __syncthreads();
-  if (tid == 0) write_features(np, sum, mxb, sm.qbin, k, feat);
+  if (tid < 32) warp_write_features(np, sum, mxb, sm.qbin, k, feat);
   __syncthreads();
 }
 
@@ -423,12 +436,13 @@ __global__ void __launch_bounds__(NT) features_kernel(const int64_t* row_ptr, co
 // ---------------------------------------------------------------------------
 // The learned bound of a batch.  Rows of up to WARP_ROW_MAX elements are done by
 // one warp each (features, network, bound: learned_short_kernel).  Longer rows
-// are listed and cut into PIECE-element pieces that the whole grid accumulates
-// (learned_piece_kernel: per-piece counts, sums and maxima, histograms added with
-// integer atomics); then one warp per long row adds its pieces in order and
-// finishes it (learned_long_kernel).  The result is the same bits every run.
+// are listed and cut into PIECE-element pieces, one warp's task each, spread over
+// the whole grid (learned_piece_kernel: per-piece counts, sums and maxima,
+// histograms added with integer atomics); then one warp per long row adds its
+// pieces' partials in a fixed order and finishes it (learned_long_kernel).  The
+// result is the same bits every run.
 // ---------------------------------------------------------------------------
-constexpr int64_t PIECE = 8192;
+constexpr int64_t PIECE = 2048;  // elements per piece of a long row: one warp's task
 
 struct LongHdr {
   unsigned long long n_long, n_pieces;  // 64-bit: no wrap even for overlapping (invalid) rows
@@ -441,23 +455,32 @@ struct PiecePart {
   double sum;
   unsigned long long mxb;
 };
+struct RowStats {  // a row's feature statistics, before the logarithms
+  int np;         // positive weights; -1: the row has no learned bound (overlapping rows)
+  int qbin[4];    // quantile bins
+  int pad;
+  double sum;
+  unsigned long long mxb;  // bits of the largest weight
+};
 struct LearnedWs {
   LongHdr* hdr;
   LongEnt* longs;
   int* piece_row;
   int* hist;  // NBINS per long row
   PiecePart* parts;
+  RowStats* stats;  // per row
   long long max_long, max_pieces;  // capacities (never reached by valid row offsets)
 };
 
 static int64_t learned_max_long(int64_t nnz) { return nnz / (WARP_ROW_MAX + 1) + 1; }
 static int64_t learned_max_pieces(int64_t nnz) { return nnz / PIECE + learned_max_long(nnz); }
-static size_t learned_ws_bytes(int64_t nnz) {
+static size_t learned_ws_bytes(int32_t n_rows, int64_t nnz) {
   const int64_t ml = learned_max_long(nnz), mp = learned_max_pieces(nnz);
   return 256 + round_up((size_t)ml * sizeof(LongEnt), 256) + round_up((size_t)mp * 4, 256) +
-         round_up((size_t)ml * NBINS * 4, 256) + round_up((size_t)mp * sizeof(PiecePart), 256);
+         round_up((size_t)ml * NBINS * 4, 256) + round_up((size_t)mp * sizeof(PiecePart), 256) +
+         round_up((size_t)n_rows * sizeof(RowStats), 256);
 }
-static LearnedWs learned_ws(unsigned char* p, int64_t nnz) {
+static LearnedWs learned_ws(unsigned char* p, int32_t n_rows, int64_t nnz) {
   const int64_t ml = learned_max_long(nnz), mp = learned_max_pieces(nnz);
   LearnedWs L;
   L.hdr = reinterpret_cast<LongHdr*>(p);
@@ -469,6 +492,8 @@ static LearnedWs learned_ws(unsigned char* p, int64_t nnz) {
   L.hist = reinterpret_cast<int*>(p);
   p += round_up((size_t)ml * NBINS * 4, 256);
   L.parts = reinterpret_cast<PiecePart*>(p);
+  p += round_up((size_t)mp * sizeof(PiecePart), 256);
+  L.stats = reinterpret_cast<RowStats*>(p);
   L.max_long = ml;
   L.max_pieces = mp;
   return L;
@@ -492,22 +517,33 @@ __device__ __forceinline__ void warp_emit_bound(const float* sp, const float* fe
   __syncwarp();
 }
 
+__device__ __forceinline__ void put_stats(RowStats* st, int np, double sum, uint64_t mxb, const int (&qbin)[4]) {
+  RowStats x;
+  x.np = np;
+  x.qbin[0] = qbin[0];
+  x.qbin[1] = qbin[1];
+  x.qbin[2] = qbin[2];
+  x.qbin[3] = qbin[3];
+  x.pad = 0;
+  x.sum = sum;
+  x.mxb = mxb;
+  *st = x;
+}
+
 __global__ void __launch_bounds__(NT) learned_short_kernel(const int64_t* row_ptr, const double* w, int n_rows,
-                                                           int64_t nnz, int k, const float* params, float margin,
-                                                           float* t_row, LearnedWs L) {
-  extern __shared__ __align__(16) float sp[];
-  __shared__ FeatSmem sm;
-  __shared__ float h1[NW][H];
-  load_params(params, sp);
-  __syncthreads();
+                                                           int64_t nnz, LearnedWs L) {
+  __shared__ int hist[NW][NBINS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * NW + warp, nw = (int64_t)gridDim.x * NW;
   for (int64_t r = gw; r < n_rows; r += nw) {
     int64_t lo, hi;
     clamp_row(row_ptr, (int)r, nnz, lo, hi);
     if (hi - lo <= WARP_ROW_MAX) {
-      warp_row_features(w, lo, hi, k, sm.hist[warp], sm.feat[warp]);
-      warp_emit_bound(sp, sm.feat[warp], h1[warp], margin, t_row, (int)r);
+      int np, qbin[4];
+      double sum;
+      uint64_t mxb;
+      warp_row_stats(w, lo, hi, hist[warp], np, sum, mxb, qbin);
+      if (lane == 0) put_stats(L.stats + r, np, sum, mxb, qbin);
       continue;
     }
     // a long row: list it, with its range of pieces, and clear its histogram.
@@ -524,7 +560,7 @@ __global__ void __launch_bounds__(NT) learned_short_kernel(const int64_t* row_pt
     const bool ok = i < L.max_long && off + np <= L.max_pieces;
     if (lane == 0) {
       if (i < L.max_long) L.longs[i] = LongEnt{ok ? (int)r : -1, (int)off, (int)np, 0};
-      if (!ok) t_row[r] = -1.0f;
+      if (!ok) L.stats[r].np = -1;
     }
     const long long pend = min(off + np, L.max_pieces);
     for (long long g = off + lane; g < pend; g += 32) L.piece_row[g] = ok ? (int)i : -1;
@@ -535,26 +571,24 @@ __global__ void __launch_bounds__(NT) learned_short_kernel(const int64_t* row_pt
 
 __global__ void __launch_bounds__(NT) learned_piece_kernel(const int64_t* row_ptr, const double* w, int64_t nnz,
                                                            LearnedWs L) {
-  __shared__ int hist[NW][NBINS];
-  __shared__ int red_i[NW];
-  __shared__ double red_s[NW];
-  __shared__ unsigned long long red_m[NW];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int hist[NW][NBINS];  // one histogram per warp: the warp's current piece
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long n_pieces = min((long long)L.hdr->n_pieces, L.max_pieces);
-  for (long long g = blockIdx.x; g < n_pieces; g += gridDim.x) {
+  int* h = hist[warp];
+  for (long long g = (long long)blockIdx.x * NW + warp; g < n_pieces; g += (long long)gridDim.x * NW) {
     const int i = L.piece_row[g];
-    if (i < 0) continue;  // uniform over the block
+    if (i < 0) continue;  // uniform over the warp
     const LongEnt e = L.longs[i];
     int64_t lo, hi;
     clamp_row(row_ptr, e.row, nnz, lo, hi);
     const int64_t plo = lo + (g - e.piece_off) * PIECE;
     const int64_t phi = min(hi, plo + PIECE);
-    for (int b = tid; b < NW * NBINS; b += NT) (&hist[0][0])[b] = 0;
-    __syncthreads();
+    for (int b = lane; b < NBINS; b += 32) h[b] = 0;
+    __syncwarp();
     int np = 0;
     ScaledSum acc{-1000000, 0.0f, 0.0f};
     uint64_t mxb = 0ull;
-    feat_scan(w, plo + tid, phi, NT, hist[warp], np, acc, mxb);
+    feat_scan(w, plo + lane, phi, 32, h, np, acc, mxb);
     double sum = ssum_value(acc);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -563,68 +597,103 @@ __global__ void __launch_bounds__(NT) learned_piece_kernel(const int64_t* row_pt
       const uint64_t o = __shfl_xor_sync(FULL, mxb, d);
       mxb = o > mxb ? o : mxb;
     }
-    if (lane == 0) {
-      red_i[warp] = np;
-      red_s[warp] = sum;
-      red_m[warp] = mxb;
-    }
-    __syncthreads();
-    for (int b = tid; b < NBINS; b += NT) {
-      int c = 0;
-#pragma unroll
-      for (int w8 = 0; w8 < NW; ++w8) c += hist[w8][b];
+    __syncwarp();
+    for (int b = lane; b < NBINS; b += 32) {
+      const int c = h[b];
       if (c) atomicAdd(&L.hist[(int64_t)i * NBINS + b], c);
     }
-    if (tid == 0) {
+    if (lane == 0) {
       PiecePart pp;
-      pp.np = 0;
+      pp.np = np;
       pp.pad = 0;
-      pp.sum = 0.0;
-      pp.mxb = 0ull;
-      for (int q = 0; q < NW; ++q) {
-        pp.np += red_i[q];
-        pp.sum += red_s[q];
-        pp.mxb = red_m[q] > pp.mxb ? red_m[q] : pp.mxb;
-      }
+      pp.sum = sum;
+      pp.mxb = mxb;
       L.parts[g] = pp;
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
-__global__ void __launch_bounds__(NT) learned_long_kernel(int k, const float* params, float margin, float* t_row,
-                                                          LearnedWs L) {
-  extern __shared__ __align__(16) float sp[];
-  __shared__ float feat[NW][F];
-  __shared__ float h1[NW][H];
+__global__ void __launch_bounds__(NT) learned_long_kernel(LearnedWs L) {
   __shared__ int hist[NW][NBINS];  // the row's histogram, staged for the quantile search
-  load_params(params, sp);
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long n_long = min((long long)L.hdr->n_long, L.max_long);
   for (long long i = (long long)blockIdx.x * NW + warp; i < n_long; i += (long long)gridDim.x * NW) {
     const LongEnt e = L.longs[i];
     if (e.row < 0) continue;  // uniform over the warp
+    // the pieces' partials: lane l adds pieces l, l + 32, ... in order, then a
+    // butterfly; a fixed order, so the same sum every run
     int np = 0;
     double sum = 0.0;
     unsigned long long mxb = 0ull;
-    if (lane == 0)
-      for (int q = 0; q < e.n_pieces; ++q) {  // in piece order: the same sum every run
-        const PiecePart pp = L.parts[e.piece_off + q];
-        np += pp.np;
-        sum += pp.sum;
-        mxb = pp.mxb > mxb ? pp.mxb : mxb;
-      }
-    np = __shfl_sync(FULL, np, 0);
+    for (int q = lane; q < e.n_pieces; q += 32) {
+      const PiecePart pp = L.parts[e.piece_off + q];
+      np += pp.np;
+      sum += pp.sum;
+      mxb = pp.mxb > mxb ? pp.mxb : mxb;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      np += __shfl_xor_sync(FULL, np, d);
+      sum += __shfl_xor_sync(FULL, sum, d);
+      const unsigned long long o = __shfl_xor_sync(FULL, mxb, d);
+      mxb = o > mxb ? o : mxb;
+    }
     const int4* g4 = reinterpret_cast<const int4*>(L.hist + i * NBINS);
     int4* s4 = reinterpret_cast<int4*>(hist[warp]);
     for (int b = lane; b < NBINS / 4; b += 32) s4[b] = __ldcg(g4 + b);
     __syncwarp();
     int qbin[4];
     warp_quantiles(hist[warp], np, qbin);
-    if (lane == 0) write_features(np, sum, mxb, qbin, k, feat[warp]);
+    if (lane == 0) put_stats(L.stats + e.row, np, sum, mxb, qbin);
     __syncwarp();
-    warp_emit_bound(sp, feat[warp], h1[warp], margin, t_row, e.row);
+  }
+}
+
+// Features, network and bound of every row from its statistics, NW rows per CTA
+// step: warp 0 takes the four logarithms of all NW rows in one pass (lane 4 q + j:
+// row q, value j of ln n+, ln sum v, ln max v, ln k; then the quantile features),
+// as a warp's FP64 instruction costs the same with one active lane as with 32;
+// then each warp runs the network on its row.
+__global__ void __launch_bounds__(NT) learned_finish_kernel(int n_rows, int k, const float* params, float margin,
+                                                            float* t_row, LearnedWs L) {
+  extern __shared__ __align__(16) float sp[];
+  __shared__ float feat[NW][F];
+  __shared__ float h1[NW][H];
+  __shared__ int npq[NW];
+  static_assert(NW * 4 == 32, "four values per row in one warp pass");
+  load_params(params, sp);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t base = (int64_t)blockIdx.x * NW; base < n_rows; base += (int64_t)gridDim.x * NW) {
+    if (warp == 0) {
+      const int q = lane >> 2, j = lane & 3;
+      const int64_t r = base + q;
+      if (r < n_rows) {
+        const RowStats st = L.stats[r];
+        if (j == 0) npq[q] = st.np;
+        if (st.np >= 0) {
+          float f = 0.0f;
+          if (st.np > 0 || j == 3) {
+            const double x = j == 0 ? (double)st.np
+                                    : (j == 1 ? st.sum : (j == 2 ? __longlong_as_double((long long)st.mxb) : (double)k));
+            f = (float)log(x);
+          }
+          feat[q][j == 3 ? 7 : j] = f;
+          const int qb = j == 0 ? st.qbin[0] : (j == 1 ? st.qbin[1] : (j == 2 ? st.qbin[2] : st.qbin[3]));
+          feat[q][3 + j] = st.np > 0 ? (float)(((double)qb + 0.5) * (0.69314718055994531 / 4.0)) : 0.0f;
+        }
+      }
+    }
+    __syncthreads();
+    const int64_t r = base + warp;
+    if (r < n_rows) {
+      if (npq[warp] >= 0)
+        warp_emit_bound(sp, feat[warp], h1[warp], margin, t_row, (int)r);
+      else if (lane == 0)
+        t_row[r] = -1.0f;  // no learned bound: the closed form
+    }
+    __syncthreads();
   }
 }
 
@@ -918,24 +987,25 @@ extern "C" int gm_model_load(float* params, const char* path, void* stream) {
   return finish(cudaStreamSynchronize(st));  // the host copy dies with this call
 }
 
-extern "C" size_t gm_learned_bound_workspace_bytes(int64_t nnz) {
-  return nnz < 0 ? 0 : learned_ws_bytes(nnz);
+extern "C" size_t gm_learned_bound_workspace_bytes(int32_t n_rows, int64_t nnz) {
+  return (nnz < 0 || n_rows < 0) ? 0 : learned_ws_bytes(n_rows, nnz);
 }
 
 static int learned_bound_launch(const int64_t* row_ptr, const double* w, int32_t n_rows, int64_t nnz, int32_t k,
                                 const float* params, float margin, float* t_row, void* workspace,
                                 cudaStream_t st) {
   if (n_rows == 0) return GM_OK;
-  const LearnedWs L = learned_ws(static_cast<unsigned char*>(workspace), nnz);
+  const LearnedWs L = learned_ws(static_cast<unsigned char*>(workspace), n_rows, nnz);
   const int grid = model_grid(1 << 30, 4);  // a full wave: the kernels stride over their work
   if (grid < 1) return GM_ECUDA;
-  if (allow_smem((const void*)learned_short_kernel, PARAM_SMEM) != GM_OK ||
-      allow_smem((const void*)learned_long_kernel, PARAM_SMEM) != GM_OK)
-    return GM_ECUDA;
+  if (allow_smem((const void*)learned_finish_kernel, PARAM_SMEM) != GM_OK) return GM_ECUDA;
   if (cudaMemsetAsync(L.hdr, 0, sizeof(LongHdr), st) != cudaSuccess) return GM_ECUDA;
-  learned_short_kernel<<<grid, NT, PARAM_SMEM, st>>>(row_ptr, w, n_rows, nnz, k, params, margin, t_row, L);
+  learned_short_kernel<<<grid, NT, 0, st>>>(row_ptr, w, n_rows, nnz, L);
   learned_piece_kernel<<<grid, NT, 0, st>>>(row_ptr, w, nnz, L);
-  learned_long_kernel<<<grid, NT, PARAM_SMEM, st>>>(k, params, margin, t_row, L);
+  learned_long_kernel<<<grid, NT, 0, st>>>(L);
+  const int fgrid = model_grid((n_rows + NW - 1) / NW, 4);
+  if (fgrid < 1) return GM_ECUDA;
+  learned_finish_kernel<<<fgrid, NT, PARAM_SMEM, st>>>(n_rows, k, params, margin, t_row, L);
   return finish(cudaGetLastError());
 }
 
@@ -946,7 +1016,7 @@ extern "C" int gm_learned_bound(const int64_t* row_ptr, const double* w, int32_t
   if (!params || !std::isfinite(margin) || !row_ptr || (n_rows > 0 && !t_out) || (nnz > 0 && !w) || !workspace ||
       !ws_aligned(workspace))
     return GM_EINVAL;
-  if (workspace_bytes < learned_ws_bytes(nnz)) return GM_ENOMEM;
+  if (workspace_bytes < learned_ws_bytes(n_rows, nnz)) return GM_ENOMEM;
   const gm::TraceRange trace("gm_learned_bound");
   return learned_bound_launch(row_ptr, w, n_rows, nnz, k, params, margin, t_out, workspace, (cudaStream_t)stream);
 }
@@ -954,7 +1024,7 @@ extern "C" int gm_learned_bound(const int64_t* row_ptr, const double* w, int32_t
 extern "C" size_t gm_sketch_learned_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k) {
   const size_t base = gm_sketch_workspace_bytes(n_rows, nnz, k, 0u);
   if (base == 0) return 0;
-  return base + round_up((size_t)n_rows * 4, 256) + learned_ws_bytes(nnz);
+  return base + round_up((size_t)n_rows * 4, 256) + learned_ws_bytes(n_rows, nnz);
 }
 
 extern "C" int gm_sketch_learned(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,

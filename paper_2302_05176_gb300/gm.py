@@ -87,7 +87,7 @@ def lib():
         L.gm_model_adam.argtypes = [_vp, _vp, _vp, ctypes.c_float, ctypes.c_int32, _vp]
         L.gm_model_save.argtypes = [_vp, ctypes.c_char_p, _vp]
         L.gm_model_load.argtypes = [_vp, ctypes.c_char_p, _vp]
-        L.gm_learned_bound_workspace_bytes.argtypes = [ctypes.c_int64]
+        L.gm_learned_bound_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64]
         L.gm_learned_bound_workspace_bytes.restype = ctypes.c_size_t
         L.gm_learned_bound.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp, ctypes.c_float,
                                        _vp, _vp, ctypes.c_size_t, _vp]
@@ -342,7 +342,8 @@ def gm_learned_bound(row_ptr, w, k, params, margin=0.0, out=None, ws=None, strea
     dev = row_ptr.device
     out = torch.empty(n_rows, dtype=torch.float32, device=dev) if out is None else out
     if ws is None:
-        ws = torch.empty(max(1, lib().gm_learned_bound_workspace_bytes(nnz)), dtype=torch.uint8, device=dev)
+        n = lib().gm_learned_bound_workspace_bytes(n_rows, nnz)
+        ws = torch.empty(max(1, n), dtype=torch.uint8, device=dev)
     _check(lib().gm_learned_bound(_ptr(row_ptr), _ptr(w), n_rows, nnz, int(k), _ptr(params), float(margin), _ptr(out),
                                   _ptr(ws), ws.numel(), _stream_handle(stream)), "gm_learned_bound")
     return out
