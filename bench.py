@@ -149,7 +149,8 @@ LEARNED_TAU = 0.95
 TRAFFIC = {"src_sha": "7d203c244297bc0d", "bytes": 167770880 + 39373568}  # k=1024 batch
 
 
-MAIN_KERNEL_SOURCES = ("gm_sketch.cu", "gm_device.cuh", "gm_arith.cuh", "gm_stream.cuh", "gm_log_tables.h",
+MAIN_KERNEL_SOURCES = ("gm_sketch.cu", "gm_fastgm_shape.cuh", "gm_device.cuh", "gm_arith.cuh", "gm_stream.cuh",
+                       "gm_log_tables.h",
                        "gm_internal.h")
 
 

@@ -47,22 +47,14 @@
 
 namespace gm {
 
-// Compile-time shape of the FastGM kernel (build-time overridable for experiments):
-// threads per CTA (CTAs per SM = 1024 / BLOCK), light-lane map capacity, lanes per
-// medium segment and its hash table.
-#ifndef GM_BLOCK
-#define GM_BLOCK 512
-#endif
+// Build-time knobs (overridable for experiments): light-lane map capacity, lanes
+// per medium segment and its hash table.  The CTA shapes are in gm_fastgm_shape.cuh.
 #ifndef GM_MAPCAP
 #define GM_MAPCAP 16
 #endif
 #ifndef GM_MED_SW
 #define GM_MED_SW 8
 #endif
-constexpr int BLOCK = GM_BLOCK;
-constexpr int WARPS = BLOCK / 32;
-constexpr int CTAS_PER_SM = 1024 / BLOCK;
-constexpr int MAPCAP = GM_MAPCAP;       // displaced positions a light lane can track
 // Default routing by the expected number of arrivals below T (gm_tuning): light
 // lanes up to LIGHT_MAX, 8-lane segments up to MEDIUM_MAX, 32-lane warps up to
 // HEAVY_MAX, dense permutations beyond; first-pass bound at quantile 1 - P_FIRST.
@@ -113,31 +105,6 @@ struct SketchArgs {
   const double* r_row;    // budget pass (plain kernel): FastSearch's R per row, else null
 };
 
-struct SmemScalars {
-  int pool, hcount, pcount, c_med, c_heavy, c_pheavy, c_super, c_psuper, unit, last;
-  float red_f[WARPS];
-  int red_i[WARPS];
-  double red_d[WARPS];
-  unsigned long long clk[WARPS][NCLK];  // light, 8-lane, 32-lane, dense, barrier wait, setup, finish, total
-};
-__shared__ SmemScalars sh_scalars;
-
-
-// Shared memory of the FastGM kernel: registers | light maps, 8-lane hashes or
-// warp hashes | ndense dense permutations | per-warp screening buffers.
-__host__ __device__ inline size_t fast_area_bytes() {
-  const size_t maps = (size_t)MAPCAP * BLOCK * 4, hashes = (size_t)WARPS * HASH_SLOTS * 4;
-  const size_t med = (size_t)WARPS * (32 / MED_SW) * MED_SLOTS * 4;
-  size_t m = maps > hashes ? maps : hashes;
-  return m > med ? m : med;
-}
-__host__ __device__ inline size_t fast_smem_bytes(int k, int ndense) {
-  return (size_t)k * sizeof(Reg) + fast_area_bytes() + (size_t)ndense * pi_stride(k) * 2 + (size_t)WARPS * 32 * 4;
-}
-// The plain kernel: registers | one dense permutation per warp.
-__host__ __device__ inline size_t plain_smem_bytes(int k) {
-  return (size_t)k * sizeof(Reg) + (size_t)WARPS * pi_stride(k) * 2;
-}
 
 __device__ __forceinline__ bool positive_finite(double v) {
   const int64_t b = (int64_t)__double_as_longlong(v);
@@ -222,216 +189,11 @@ __device__ __forceinline__ void seg_phase(const SketchArgs& a, int64_t lo, uint6
   }
 }
 
-// --------------------------------------------------------------------------
-// Light path with warp screening.  Elements [lo, lo+n) of the unit; T as bits and
-// as an FP32 value (equal as reals).  Elements expected to need more than
-// a.light_max arrivals go to the work list, tagged by their expected count.
-// --------------------------------------------------------------------------
-template <int ARITH>
-__device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int n, uint64_t Tbits, float Tf,
-                                            Reg* regs, uint32_t* map, uint32_t* wbuf, SmemScalars& sh,
-                                            Counters& cnt, bool& gave_up) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int k = a.k;
-  const float kf = (float)k;
-  int e = -1, z = 0, msize = 0;
-  int32_t id = 0;
-  double R = 0.0;
-  Fix acc = fix_zero();
-  int wcount = 0;
-  bool pool_done = false;
-  while (true) {
-    // hand survivors to idle lanes, screening new elements while some are idle
-    uint32_t nmask = __ballot_sync(FULL, e < 0);
-    while (nmask && !(pool_done && wcount == 0)) {
-      if (wcount == 0) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&sh.pool, 32);
-        base = __shfl_sync(FULL, base, 0);
-        if (base >= n) {
-          pool_done = true;
-          break;
-        }
-        const int slot = base + lane;
-        bool surv = false;
-        if (slot < n) {
-          const double v = a.w[lo + slot];
-          if (positive_finite(v)) {
-            ++cnt.elements;
-            const float vf = f32_trunc(v);
-            const float lam = kf * (1.0f - __expf(-(vf * Tf)));  // expected arrivals <= T (routing only)
-            if (lam > a.light_max) {
-              const uint32_t tag = lam > a.heavy_max ? TAG_SUPER : (lam > a.medium_max ? TAG_HEAVY : TAG_MEDIUM);
-              a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | tag;
-            } else {
-              const Words wd = philox((uint32_t)a.ids[lo + slot], 0u, a.key0, a.key1);
-              if (screen_out(wd.w1, vf, Tf, kf))
-                ++cnt.screened;  // first arrival certainly above T: nothing of it counts
-              else
-                surv = true;
-            }
-          }
-        }
-        const uint32_t sm = __ballot_sync(FULL, surv);
-        if (surv) wbuf[__popc(sm & lanemask_lt())] = (uint32_t)slot;
-        wcount = __popc(sm);
-        __syncwarp();
-        continue;
-      }
-      const int take = min(__popc(nmask), wcount);
-      const int rank = __popc(nmask & lanemask_lt());
-      if (e < 0 && rank < take) {
-        e = (int)wbuf[wcount - 1 - rank];
-        const int64_t g = lo + e;
-        id = a.ids[g];
-        R = arr_rcp<ARITH>(a.w[g]);
-        z = 0;
-        acc = fix_zero();
-        msize = 0;
-      }
-      wcount -= take;
-      __syncwarp();
-      nmask = __ballot_sync(FULL, e < 0);
-    }
-    if (!__any_sync(FULL, e >= 0)) break;  // nothing left to stream
-    if (e < 0) continue;
-    int J;
-    fix_add(acc, arrival_term<ARITH>(id, z, k, a.key0, a.key1, a.ctab, J));
-    const uint64_t bb = (uint64_t)__double_as_longlong(arr_mul<ARITH>(fix_round(acc), R));
-    ++cnt.arrivals;
-    if (bb > Tbits) {  // FastPrune: the rest of this stream is above the bound
-      e = -1;
-      continue;
-    }
-    // Fisher-Yates step z on the sparse map (positions < z are final and dropped)
-    int iz = -1;
-    for (int i = 0; i < msize; ++i)
-      if ((map[i * BLOCK + tid] >> 16) == (uint32_t)z) {
-        iz = i;
-        break;
-      }
-    uint32_t vz = (uint32_t)z;
-    if (iz >= 0) {
-      vz = map[iz * BLOCK + tid] & 0xFFFFu;
-      --msize;
-      map[iz * BLOCK + tid] = map[msize * BLOCK + tid];
-    }
-    uint32_t c = vz;
-    bool overflow = false;
-    if (J != z) {
-      int ij = -1;
-      for (int i = 0; i < msize; ++i)
-        if ((map[i * BLOCK + tid] >> 16) == (uint32_t)J) {
-          ij = i;
-          break;
-        }
-      if (ij >= 0) {
-        c = map[ij * BLOCK + tid] & 0xFFFFu;
-        map[ij * BLOCK + tid] = ((uint32_t)J << 16) | vz;
-      } else {
-        c = (uint32_t)J;
-        if (msize >= MAPCAP) {
-          overflow = true;
-        } else {
-          map[msize * BLOCK + tid] = ((uint32_t)J << 16) | vz;
-          ++msize;
-        }
-      }
-    }
-    if (overflow) {  // restart this element on an 8-lane segment (updates are idempotent)
-      a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)e | TAG_MEDIUM;
-      e = -1;
-      continue;
-    }
-    cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
-    ++cnt.kept;
-    if (++z >= k) e = -1;
-  }
-}
-
 // SM clock, ordered with the surrounding memory operations and barriers.
 __device__ __forceinline__ long long read_clock() {
   long long c;
   asm volatile("mov.u64 %0, %%clock64;" : "=l"(c) : : "memory");
   return c;
-}
-
-__device__ __forceinline__ void clk_add(Counters&, int which, long long& t) {
-  const long long now = read_clock();
-  if ((threadIdx.x & 31) == 0) sh_scalars.clk[threadIdx.x >> 5][which] += (unsigned long long)(now - t);
-  t = now;
-}
-
-// All warp-path classes of one pass: 8-lane segments, then without a barrier
-// the 32-lane warps' share of the work list (a warp's hash region is the same
-// in both), then the elements promoted out of 8-lane segments, then dense
-// permutations (warps < ndense).  (Lowering T to the running y* at the barriers
-// saved 2 % of the arrivals and cost more in barriers: measured and dropped.)
-template <int ARITH>
-__device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uint64_t Tbits, Reg* regs,
-                                            uint32_t* area, uint16_t* dense, SmemScalars& sh, Counters& cnt,
-                                            bool& gave_up, long long& t) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nh = sh.hcount;
-  {
-    const int seg = lane / MED_SW;
-    const HashPiN<MED_SLOTS> hp{area + (warp * (32 / MED_SW) + seg) * MED_SLOTS};
-    seg_phase<ARITH, MED_SW>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_med, TAG_MEDIUM, hp, MED_MAX_FILL,
-                             a.plist + lo, &sh.pcount, cnt, gave_up);
-  }
-  clk_add(cnt, CLK_MEDIUM, t);
-  // a warp's hash region is the same in both phases: the heavy list needs no barrier
-  {
-    const HashPi hp{area + warp * HASH_SLOTS};
-    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_heavy, TAG_HEAVY, hp, HASH_MAX_FILL, nullptr,
-                         nullptr, cnt, gave_up);
-  }
-  clk_add(cnt, CLK_HEAVY, t);
-  __syncthreads();  // every promotion is listed
-  clk_add(cnt, CLK_WAIT, t);
-  {
-    const HashPi hp{area + warp * HASH_SLOTS};
-    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_pheavy, TAG_HEAVY, hp, HASH_MAX_FILL,
-                         nullptr, nullptr, cnt, gave_up);
-  }
-  clk_add(cnt, CLK_HEAVY, t);
-  __syncthreads();
-  clk_add(cnt, CLK_WAIT, t);
-  // dense permutations: the CTA's own, then as many as fit in the (now idle) hash area
-  const int ndense = min(WARPS, a.ndense + (int)(fast_area_bytes() / (pi_stride(a.k) * 2)));
-  if (warp < ndense) {
-    uint16_t* mine = warp < a.ndense ? dense + (size_t)warp * pi_stride(a.k)
-                                     : reinterpret_cast<uint16_t*>(area) + (size_t)(warp - a.ndense) * pi_stride(a.k);
-    const DensePi dp{mine};
-    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_super, TAG_SUPER, dp, 1 << 30, nullptr,
-                         nullptr, cnt, gave_up);
-    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_psuper, TAG_SUPER, dp, 1 << 30,
-                         nullptr, nullptr, cnt, gave_up);
-  }
-  clk_add(cnt, CLK_SUPER, t);
-  __syncthreads();
-  clk_add(cnt, CLK_WAIT, t);
-}
-
-__device__ __forceinline__ void reset_lists(SmemScalars& sh) {
-  if (threadIdx.x == 0) {
-    sh.pool = 0;
-    sh.hcount = 0;
-    sh.pcount = 0;
-    sh.c_med = sh.c_heavy = sh.c_pheavy = sh.c_super = sh.c_psuper = 0;
-  }
-}
-
-__device__ __forceinline__ void init_regs(const SketchArgs& a, Reg* regs, int k) {
-  for (int j = threadIdx.x; j < k; j += BLOCK) {
-    if (a.init_y) {  // a running sketch: (+inf, -1) is an unfilled register
-      regs[j].y = (uint64_t)__double_as_longlong(a.init_y[j]);
-      regs[j].id = a.init_s[j] < 0 ? UNFILLED_ID : (uint64_t)(uint32_t)a.init_s[j];
-    } else {
-      regs[j].y = INF_BITS;
-      regs[j].id = UNFILLED_ID;
-    }
-  }
 }
 
 // A row's first-pass bound from the per-row table: an absolute bound, or (when
@@ -450,17 +212,6 @@ __device__ __forceinline__ void chunk_bound(const SketchArgs& a, int row, float 
   const bool none = !(Tf < 3.0e38f);
   Tbits = none ? DBL_MAX_BITS : (uint64_t)__double_as_longlong(f64_from_f32(Tf));
   if (none) Tf = __int_as_float(0x7F800000);
-}
-
-__device__ __forceinline__ void write_out(const SketchArgs& a, int row, const Reg* regs) {
-  const int k = a.k;
-  int32_t* s = a.s_out + (int64_t)row * k;
-  double* y = a.y_out + (int64_t)row * k;
-  for (int j = threadIdx.x; j < k; j += BLOCK) {
-    const Reg r = regs[j];
-    s[j] = (r.id == UNFILLED_ID) ? -1 : (int32_t)r.id;
-    y[j] = __longlong_as_double((long long)r.y);
-  }
 }
 
 // Row bounds clamped to [0, nnz] so malformed row_ptr never leads out of range.
@@ -537,23 +288,6 @@ __device__ __forceinline__ void block_sum(const SketchArgs& a, int64_t lo, int n
   __syncthreads();
 }
 
-__device__ __forceinline__ void flush_counters(const SketchArgs& a, Counters& cnt, bool gave_up) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t v32[8] = {cnt.arrivals, cnt.elements, cnt.screened, cnt.heavy,
-                           cnt.escalated, cnt.cas, cnt.kept, cnt.fallback};
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    unsigned long long v = v32[q];
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
-    if (lane == 0 && v) atomicAdd(&a.hdr->counters[q < 6 ? q : 6 + NCLK + (q - 6)], v);
-  }
-  if (lane == 0)
-    for (int q = 0; q < NCLK; ++q)
-      if (sh_scalars.clk[threadIdx.x >> 5][q]) atomicAdd(&a.hdr->counters[6 + q], sh_scalars.clk[threadIdx.x >> 5][q]);
-  if (gave_up) atomicOr(&a.hdr->status, WS_ETIMEOUT);
-}
-
 // 128-bit compare-and-swap minimum on a global register (the union of Sec. 2.3).
 __device__ __forceinline__ void global_lower(Reg* r, uint64_t yb, uint64_t id, bool& gave_up) {
   uint64_t cy = __ldcg(&r->y), cid = __ldcg(&r->id);
@@ -601,264 +335,10 @@ __device__ __forceinline__ void resolve_unit(const SketchArgs& a, uint32_t u, ui
   }
 }
 
-// One row (short, or a long row being redone) by one CTA: passes with a growing
-// bound from `first_pass` on, until every register is filled.
-template <int ARITH>
-__device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t lo, int n, int first_pass, Reg* regs,
-                                           uint32_t* area, uint16_t* dense, uint32_t* wbuf, SmemScalars& sh,
-                                           Counters& cnt, bool& gave_up) {
-  const int tid = threadIdx.x;
-  float sumv;
-  int npos;
-  long long t = read_clock();
-  block_sum<BLOCK>(a, lo, n, sh.red_f, sh.red_i, sumv, npos);
-  clk_add(cnt, CLK_SETUP, t);
-  for (int pass = first_pass; npos > 0; ++pass) {
-    float Tf = a.q2 / sumv;
-    if (pass == 0 && !row_bound(a, row, Tf)) Tf = a.q1 / sumv;
-    double Td = 0.0;
-    bool last = !(Tf < 3.0e38f) || pass >= 12;
-    if (!last) {
-      Td = f64_from_f32(Tf);
-      for (int p = 1; p < pass; ++p) {  // passes >= 2 widen the bound by 16x each
-        Td *= 16.0;
-        Tf *= 16.0f;  // exact: the screen needs Tf = Td as reals, so no clamp below Td
-      }
-      if (!(Td < 1.0e300) || !(Tf < 3.0e38f)) last = true;
-    }
-    const uint64_t Tbits = last ? DBL_MAX_BITS : (uint64_t)__double_as_longlong(Td);
-    if (last) Tf = __int_as_float(0x7F800000);  // +inf: no screening, everything streams
-    reset_lists(sh);
-    __syncthreads();
-    clk_add(cnt, CLK_SETUP, t);
-    light_phase<ARITH>(a, lo, n, Tbits, Tf, regs, area, wbuf + (tid >> 5) * 32, sh, cnt, gave_up);
-    clk_add(cnt, CLK_LIGHT, t);
-    __syncthreads();
-    clk_add(cnt, CLK_WAIT, t);
-    warp_phases<ARITH>(a, lo, Tbits, regs, area, dense, sh, cnt, gave_up, t);
-    // a register above T may still be lowered by an arrival above T: redo wider.
-    // (Without a starting sketch that is exactly an unfilled register.)
-    int empty = 0;
-    for (int j = tid; j < a.k; j += BLOCK) empty |= (regs[j].y > Tbits);
-    const bool again = __syncthreads_or(empty) && !last;
-    clk_add(cnt, CLK_FINISH, t);
-    if (!again) break;
-    if (tid == 0) {
-      ++cnt.escalated;
-      if (pass == 0) ++cnt.fallback;
-    }
-  }
-  write_out(a, row, regs);
-  clk_add(cnt, CLK_FINISH, t);
-}
-
-// A long row's last finished chunk: read the merged registers; write the row,
-// or queue it for a single-CTA redo with a larger bound.
-__device__ __forceinline__ void finish_long(const SketchArgs& a, int row, int longi, SmemScalars& sh) {
-  const int k = a.k;
-  const Reg* g = a.long_regs + (int64_t)longi * k;
-  uint64_t Tbits;
-  float Tf;
-  chunk_bound(a, row, a.longs[longi].sum, Tbits, Tf);
-  int empty = 0;
-  for (int j = threadIdx.x; j < k; j += BLOCK) empty |= (__ldcg(&g[j].y) > Tbits);
-  const bool any_empty = __syncthreads_or(empty) != 0;
-  const bool has_pos = a.longs[longi].npos > 0;
-  if (any_empty && has_pos && isfinite(a.q_split)) {
-    if (threadIdx.x == 0) a.esc[atomicAdd(&a.hdr->esc_count, 1u)] = (uint32_t)row;
-    return;
-  }
-  int32_t* s = a.s_out + (int64_t)row * k;
-  double* y = a.y_out + (int64_t)row * k;
-  for (int j = threadIdx.x; j < k; j += BLOCK) {
-    const uint64_t yb = __ldcg(&g[j].y), id = __ldcg(&g[j].id);
-    s[j] = (id == UNFILLED_ID) ? -1 : (int32_t)id;
-    y[j] = __longlong_as_double((long long)yb);
-  }
-}
-
 // MODE_MAIN: all units.  MODE_ESC: the long rows queued for a redo, one CTA each.
 constexpr int MODE_MAIN = 0;
 constexpr int MODE_ESC = 1;
 
-template <int ARITH, int MODE>
-__global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  SmemScalars& sh = sh_scalars;
-  const int k = a.k;
-  Reg* regs = reinterpret_cast<Reg*>(smem);
-  uint32_t* area = reinterpret_cast<uint32_t*>(smem + (size_t)k * sizeof(Reg));
-  uint16_t* dense = reinterpret_cast<uint16_t*>(smem + (size_t)k * sizeof(Reg) + fast_area_bytes());
-  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem + (size_t)k * sizeof(Reg) + fast_area_bytes() +
-                                               (size_t)a.ndense * pi_stride(k) * 2);
-  const int tid = threadIdx.x;
-  Counters cnt;
-  cnt.zero();
-  bool gave_up = false;
-  const long long t_start = read_clock();
-  if ((tid & 31) == 0)
-    for (int q = 0; q < NCLK; ++q) sh.clk[tid >> 5][q] = 0ull;
-  const uint32_t n_extra = a.hdr->n_extra, n_long = a.hdr->n_long;
-  const uint32_t n_units = MODE == MODE_MAIN ? n_extra + (uint32_t)a.n_rows : a.hdr->esc_count;
-
-  while (true) {
-    if (tid == 0) sh.unit = (int)atomicAdd(MODE == MODE_MAIN ? &a.hdr->unit_counter : &a.hdr->esc_counter, 1u);
-    __syncthreads();
-    const uint32_t u = (uint32_t)sh.unit;
-    if (u >= n_units) break;
-    int row, chunk, longi;
-    if (MODE == MODE_ESC) {
-      row = (int)a.esc[u];
-      chunk = 0;
-      longi = -1;
-    } else {
-      resolve_unit(a, u, n_extra, n_long, row, chunk, longi);
-    }
-    int64_t lo, hi;
-    row_bounds(a, row, lo, hi);
-    init_regs(a, regs, k);
-    if (longi < 0) {  // the whole row in this CTA
-      fastgm_row<ARITH>(a, row, lo, (int)(hi - lo), MODE == MODE_ESC ? 1 : 0, regs, area, dense, wbuf, sh, cnt,
-                        gave_up);
-      __syncthreads();
-      continue;
-    }
-    // one chunk of a long row, bound from the row's sum (rowsum kernel)
-    const int64_t clo = lo + (int64_t)chunk * SPLIT_LEN;
-    const int64_t chi = min(hi, clo + SPLIT_LEN);
-    const LongRow lr = a.longs[longi];
-    if (lr.npos > 0 && chi > clo) {
-      uint64_t Tbits;
-      float Tf;
-      chunk_bound(a, row, lr.sum, Tbits, Tf);
-      reset_lists(sh);
-      __syncthreads();
-      long long t = read_clock();
-      light_phase<ARITH>(a, clo, (int)(chi - clo), Tbits, Tf, regs, area, wbuf + (tid >> 5) * 32, sh, cnt, gave_up);
-      clk_add(cnt, CLK_LIGHT, t);
-      __syncthreads();
-      clk_add(cnt, CLK_WAIT, t);
-      warp_phases<ARITH>(a, clo, Tbits, regs, area, dense, sh, cnt, gave_up, t);
-      Reg* g = a.long_regs + (int64_t)longi * k;
-      for (int j = tid; j < k; j += BLOCK) {
-        const Reg r = regs[j];
-        if (r.y != INF_BITS) global_lower(&g[j], r.y, r.id, gave_up);
-      }
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) sh.last = (atomicAdd(&a.longs[longi].done, 1u) == lr.nchunks - 1) ? 1 : 0;
-    __syncthreads();
-    if (sh.last) {
-      __threadfence();
-      finish_long(a, row, longi, sh);
-    }
-    __syncthreads();
-  }
-  if ((tid & 31) == 0) sh_scalars.clk[tid >> 5][CLK_TOTAL] += (unsigned long long)(read_clock() - t_start);
-  __syncwarp();
-  flush_counters(a, cnt, gave_up);
-}
-
-// The plain sketch: every positive element, all k arrivals, warp path with one
-// dense permutation per warp.  Long rows are chunked and merged like FastGM's.
-template <int ARITH>
-__global__ void __launch_bounds__(BLOCK, 1) plain_kernel(SketchArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  SmemScalars& sh = sh_scalars;
-  const int k = a.k;
-  Reg* regs = reinterpret_cast<Reg*>(smem);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const DensePi dp{reinterpret_cast<uint16_t*>(smem + (size_t)k * sizeof(Reg)) + (size_t)warp * pi_stride(k)};
-  Counters cnt;
-  cnt.zero();
-  bool gave_up = false;
-  const uint32_t n_extra = a.hdr->n_extra, n_long = a.hdr->n_long;
-  const uint32_t n_units = n_extra + (uint32_t)a.n_rows;
-  while (true) {
-    if (tid == 0) sh.unit = (int)atomicAdd(&a.hdr->unit_counter, 1u);
-    __syncthreads();
-    const uint32_t u = (uint32_t)sh.unit;
-    if (u >= n_units) break;
-    int row, chunk, longi;
-    resolve_unit(a, u, n_extra, n_long, row, chunk, longi);
-    int64_t lo, hi;
-    row_bounds(a, row, lo, hi);
-    init_regs(a, regs, k);
-    const int64_t clo = longi < 0 ? lo : lo + (int64_t)chunk * SPLIT_LEN;
-    const int64_t chi = longi < 0 ? hi : min(hi, clo + SPLIT_LEN);
-    const int n = (int)(chi - clo);
-    if (longi < 0) {
-      float sumv;
-      int npos;
-      block_sum<BLOCK>(a, lo, n, sh.red_f, sh.red_i, sumv, npos);  // validation only
-    }
-    // budget pass (FastSearch, Algorithm 1): element i releases ceil(R v_i / sum v)
-    // of its arrivals, the ratio and product in FP64 as the paper's schedule states
-    double Rr = 0.0, dsum = 0.0;
-    if (a.r_row) {
-      Rr = a.r_row[row];
-      dsum = longi < 0 ? block_dsum<BLOCK>(a.w, lo, n, sh.red_d) : __ldcg(&a.longs[longi].dsum);
-    }
-    if (tid == 0) sh.pool = 0;
-    __syncthreads();
-    while (true) {
-      int slot = 0;
-      if (lane == 0) slot = atomicAdd(&sh.pool, 1);
-      slot = __shfl_sync(FULL, slot, 0);
-      if (slot >= n) break;
-      const double v = a.w[clo + slot];
-      if (!positive_finite(v)) continue;
-      if (lane == 0) ++cnt.elements;
-      const int32_t id = a.ids[clo + slot];
-      const double R = arr_rcp<ARITH>(v);
-      int lim = k;
-      if (a.r_row) {
-        const double b = ceil(__dmul_rn(Rr, __ddiv_rn(v, dsum)));
-        lim = b < (double)k ? (int)b : k;
-      }
-      dp.reset(k, lane);
-      Fix carry = fix_zero();
-      for (int z0 = 0; z0 < lim; z0 += 32) {  // all k arrivals (or the budget), 32 per step
-        int J, c;
-        const uint64_t bb = warp_batch<ARITH>(id, R, z0, k, a.key0, a.key1, a.ctab, carry, lane, J);
-        const int nz = min(32, lim - z0);
-        if (lane == 0) cnt.arrivals += (uint32_t)nz;
-        warp_fy_steps(dp, z0, J, nz, lane, c);
-        if (lane < nz && bb <= DBL_MAX_BITS) {
-          cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
-          ++cnt.kept;
-        }
-      }
-    }
-    __syncthreads();
-    if (longi < 0) {
-      write_out(a, row, regs);
-      __syncthreads();
-      continue;
-    }
-    Reg* g = a.long_regs + (int64_t)longi * k;
-    for (int j = tid; j < k; j += BLOCK) {
-      const Reg r = regs[j];
-      if (r.y != INF_BITS) global_lower(&g[j], r.y, r.id, gave_up);
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) sh.last = (atomicAdd(&a.longs[longi].done, 1u) == a.longs[longi].nchunks - 1) ? 1 : 0;
-    __syncthreads();
-    if (sh.last) {
-      __threadfence();
-      const Reg* gg = a.long_regs + (int64_t)longi * k;
-      for (int j = tid; j < k; j += BLOCK) {
-        const uint64_t yb = __ldcg(&gg[j].y), id = __ldcg(&gg[j].id);
-        a.s_out[(int64_t)row * k + j] = (id == UNFILLED_ID) ? -1 : (int32_t)id;
-        a.y_out[(int64_t)row * k + j] = __longlong_as_double((long long)yb);
-      }
-    }
-    __syncthreads();
-  }
-  flush_counters(a, cnt, gave_up);
-}
 
 // C_z = RN(1 / (k - z)); zero the header; check the row_ptr end points.
 __global__ void init_kernel(WsHeader* hdr, double* ctab, int k, const int64_t* row_ptr, int n_rows, int64_t nnz,
@@ -979,15 +459,6 @@ __global__ void __launch_bounds__(256) longprep_kernel(SketchArgs a) {
   }
 }
 
-// Dense permutations per CTA: as many as fit with two CTAs per SM (at least one).
-static int dense_buffers(int k, size_t smem_per_sm) {
-  const size_t budget = smem_per_sm / CTAS_PER_SM - 2048;  // each CTA with ~1 KB reserved and static smem
-  const size_t base = fast_smem_bytes(k, 0);
-  if (budget <= base + pi_stride(k) * 2) return 1;
-  const size_t n = (budget - base) / (pi_stride(k) * 2);
-  return (int)(n < 1 ? 1 : (n > (size_t)WARPS ? (size_t)WARPS : n));
-}
-
 static double quantile_bound(double p, int k) {
   // (1 - p) quantile of max of k iid Exp(1):  -ln(1 - (1 - p)^(1/k))
   return -std::log(-std::expm1(std::log1p(-p) / (double)k));
@@ -1015,47 +486,34 @@ static int allow_max_smem(const void* kern) {
   return GM_OK;
 }
 
-template <class KERNEL>
-static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
-  int per_sm = 0;
-  if (allow_max_smem((const void*)kern) != GM_OK) return GM_ECUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, sm) != cudaSuccess) return GM_ECUDA;
-  if (per_sm < 1) return GM_EINVAL;
-  grid = nsm * per_sm;
-  if (grid > cap) grid = cap;
-  if (grid < 1) grid = 1;
-  return GM_OK;
-}
-
 // Optional events recorded around the main FastGM (or plain) kernel launch, for
 // timing that kernel alone on the call's stream (gm_diag_time_main_kernel).
 static cudaEvent_t g_main_before = nullptr, g_main_after = nullptr;
 
+
+#define GM_SHAPE_NS s512
+#define GM_SHAPE_BLOCK 512
+#include "gm_fastgm_shape.cuh"
+#undef GM_SHAPE_NS
+#undef GM_SHAPE_BLOCK
+#define GM_SHAPE_NS s1024
+#define GM_SHAPE_BLOCK 1024
+#include "gm_fastgm_shape.cuh"
+#undef GM_SHAPE_NS
+#undef GM_SHAPE_BLOCK
+
+// Rows of k >= WIDE_K registers go to 1024-thread CTAs, one per SM: twice the
+// warps on a row and the SM's whole shared memory for its permutations (measured
+// at k = 4096: 9.83 ms per 4,096-row batch against 11.28 with two 512-thread
+// CTAs; at k = 1024: 3.25 against 2.89).  The default arithmetic only; the
+// others and the plain sketch keep 512-thread CTAs.
+constexpr int WIDE_K = 4096;
+
 template <int ARITH>
-static int launch_all(const SketchArgs& a, bool plain, int nsm, cudaStream_t stream) {
-  const size_t sm = plain ? plain_smem_bytes(a.k) : fast_smem_bytes(a.k, a.ndense);
-  const int max_units = a.n_rows + (int)((a.nnz + SPLIT_LEN - 1) / SPLIT_LEN);
-  plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);
-  longprep_kernel<<<nsm * 4, 256, 0, stream>>>(a);
-  int grid = 0, rc;
-  if (plain) {
-    rc = occupancy_grid(plain_kernel<ARITH>, sm, nsm, max_units, grid);
-    if (rc != GM_OK) return rc;
-    if (g_main_before) cudaEventRecord(g_main_before, stream);
-    plain_kernel<ARITH><<<grid, BLOCK, sm, stream>>>(a);
-    if (g_main_after) cudaEventRecord(g_main_after, stream);
-    return GM_OK;
-  }
-  rc = occupancy_grid(fastgm_kernel<ARITH, MODE_MAIN>, sm, nsm, max_units, grid);
-  if (rc != GM_OK) return rc;
-  if (g_main_before) cudaEventRecord(g_main_before, stream);
-  fastgm_kernel<ARITH, MODE_MAIN><<<grid, BLOCK, sm, stream>>>(a);
-  if (g_main_after) cudaEventRecord(g_main_after, stream);
-  int grid_esc = 0;
-  rc = occupancy_grid(fastgm_kernel<ARITH, MODE_ESC>, sm, nsm, a.max_long, grid_esc);
-  if (rc != GM_OK) return rc;
-  fastgm_kernel<ARITH, MODE_ESC><<<grid_esc, BLOCK, sm, stream>>>(a);
-  return GM_OK;
+static int launch_shape(const SketchArgs& a, bool plain, int nsm, size_t smem_per_sm, cudaStream_t stream) {
+  if constexpr (ARITH == ARITH_MIX)
+    if (!plain && a.k >= WIDE_K) return s1024::launch<ARITH>(a, plain, nsm, smem_per_sm, stream);
+  return s512::launch<ARITH>(a, plain, nsm, smem_per_sm, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -1164,10 +622,10 @@ static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GM_ECUDA;
   if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
     return GM_ECUDA;
-  a.ndense = dense_buffers(k, (size_t)smem_sm);
-  const int rc = (flags & GM_FLAG_FP64_UNIT)      ? launch_all<ARITH_FP64>(a, plain, nsm, stream)
-                 : (flags & GM_FLAG_INT_PRODUCTS) ? launch_all<ARITH_INT>(a, plain, nsm, stream)
-                                                  : launch_all<ARITH_MIX>(a, plain, nsm, stream);
+  const size_t smem = (size_t)smem_sm;
+  const int rc = (flags & GM_FLAG_FP64_UNIT)      ? launch_shape<ARITH_FP64>(a, plain, nsm, smem, stream)
+                 : (flags & GM_FLAG_INT_PRODUCTS) ? launch_shape<ARITH_INT>(a, plain, nsm, smem, stream)
+                                                  : launch_shape<ARITH_MIX>(a, plain, nsm, smem, stream);
   if (rc != GM_OK) return rc;
   return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
 }
