@@ -507,7 +507,10 @@ static cudaEvent_t g_main_before = nullptr, g_main_after = nullptr;
 // at k = 4096: 9.83 ms per 4,096-row batch against 11.28 with two 512-thread
 // CTAs; at k = 1024: 3.25 against 2.89).  The default arithmetic only; the
 // others and the plain sketch keep 512-thread CTAs.
-constexpr int WIDE_K = 4096;
+#ifndef GM_WIDE_K
+#define GM_WIDE_K 4096
+#endif
+constexpr int WIDE_K = GM_WIDE_K;
 
 template <int ARITH>
 static int launch_shape(const SketchArgs& a, bool plain, int nsm, size_t smem_per_sm, cudaStream_t stream) {
