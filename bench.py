@@ -146,7 +146,7 @@ LAUNCHES_PER_CALL = 5                           # init, plan, long-row prep, mai
 LEARNED_TAU = 0.95
 # DRAM bytes (read + write) of one main-kernel launch from ncu, valid only for the
 # kernel sources they were taken on (sha256 of csrc/, see kernel_source_sha).
-TRAFFIC = {"src_sha": "63ad0d3555797d2e", "bytes": 166921472 + 41164544}  # k=1024 batch
+TRAFFIC = {"src_sha": "aba465500c6a622a", "bytes": 166921472 + 41164544}  # k=1024 batch
 
 
 MAIN_KERNEL_SOURCES = ("gm_sketch.cu", "gm_fastgm_shape.cuh", "gm_device.cuh", "gm_arith.cuh", "gm_stream.cuh",
@@ -155,13 +155,20 @@ MAIN_KERNEL_SOURCES = ("gm_sketch.cu", "gm_fastgm_shape.cuh", "gm_device.cuh", "
 
 
 def kernel_source_sha():
-    """sha256 (16 hex digits) of the sources the main sketch kernel is compiled from."""
+    """sha256 (16 hex digits) of the code the main sketch kernel is compiled from:
+    its sources with comments and blank lines removed, so that a comment-only edit
+    keeps a recorded traffic capture valid."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2302_05176_gb300", "csrc")
     for name in MAIN_KERNEL_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(name.encode() + b"\0" + f.read())
+        with open(os.path.join(csrc, name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.split("\n")]
+        code = "\n".join(ln for ln in lines if ln.strip())
+        h.update(name.encode() + b"\0" + code.encode())
     return h.hexdigest()[:16]
 
 

@@ -1,9 +1,11 @@
 // gm_sketch.cu -- FastGM (Algorithm 1, Sec. 2.2) and the plain O(k n+) sketch on GB300.
 //
 // Work is cut into units: one per row, plus one per extra chunk of SPLIT_LEN
-// elements of a long row.  A persistent grid of 512-thread CTAs takes units from
-// a counter (long-row chunks first).  The k registers of a unit live in shared
-// memory as 16-byte (y, id) pairs lowered by 128-bit compare-and-swap; the units
+// elements of a long row.  A persistent grid of CTAs (two of 512 threads per SM,
+// or one of 1024 at k = 4096; the kernels for both shapes come from
+// gm_fastgm_shape.cuh) takes units from a counter (long-row chunks first).  The
+// k registers of a unit live in shared memory as 16-byte (y, id) pairs lowered
+// by 128-bit compare-and-swap; the units
 // of a long row then merge their registers into global memory with the same
 // compare-and-swap, the union of Sec. 2.3 (Mergeability), and the last one writes
 // the row.
