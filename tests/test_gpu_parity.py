@@ -228,6 +228,25 @@ def test_lognormal_batch_full_size_sampled_rows():
         assert np.isin(s[r], X.row(r)[0]).all()
 
 
+def test_lognormal_batch_full_size_k4096_sampled_rows():
+    """The same 4,096-row batch at k = 4096, the benchmark's second launch (1024-thread
+    CTAs): sampled rows against the oracle, every row bit-identical to the
+    512-thread shape (the all-integer arithmetic runs there), all registers filled."""
+    X = W.lognormal_batch(seed=1)
+    k, seed = 4096, 1
+    s, y, _ = run(gm.gm_sketch, X, k, seed, flags=0)
+    s_i, y_i, _ = run(gm.gm_sketch, X, k, seed, flags=gm.GM_FLAG_INT_PRODUCTS)
+    assert np.array_equal(s, s_i) and np.array_equal(y.view(np.int64), y_i.view(np.int64))
+    lens = np.diff(X.row_ptr)
+    order = np.argsort(lens)
+    rng = np.random.default_rng(1)
+    sample = np.unique(np.concatenate([order[:3], rng.choice(np.flatnonzero(lens < 1500), size=4, replace=False)]))
+    s_ref, y_ref, y2_ref = oracle.sketch_rows_parallel(X.row_ptr, X.ids, X.w, k, seed, sample, want_y2=True)
+    rep = compare_sketch(s[sample], y[sample], s_ref, y_ref, y2_ref)
+    assert rep["ok"], rep
+    assert np.all(np.isfinite(y)) and np.all(y > 0)
+
+
 def test_pareto_heavy_full_size():
     """16 rows x 10^6 elements, Pareto(1.2, x_min 1e-3), k = 4096, seed 1: the heavy-tail
     launch the benchmark times.  FastGM equals the plain O(k n+) sketch on every
