@@ -522,6 +522,7 @@ __global__ void __launch_bounds__(BLOCK, 1) plain_kernel(SketchArgs a) {
   }
   flush_counters(a, cnt, gave_up);
 }
+
 // Dense permutations per CTA: as many as fit with CTAS_PER_SM CTAs per SM (at least one).
 static int dense_buffers(int k, size_t smem_per_sm) {
   const size_t budget = smem_per_sm / CTAS_PER_SM - 2048;  // each CTA with ~1 KB reserved and static smem
@@ -530,6 +531,7 @@ static int dense_buffers(int k, size_t smem_per_sm) {
   const size_t n = (budget - base) / (pi_stride(k) * 2);
   return (int)(n < 1 ? 1 : (n > (size_t)WARPS ? (size_t)WARPS : n));
 }
+
 template <class KERNEL>
 static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
   int per_sm = 0;
@@ -541,6 +543,7 @@ static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
   if (grid < 1) grid = 1;
   return GM_OK;
 }
+
 template <int ARITH>
 static int launch_all(const SketchArgs& a, bool plain, int nsm, cudaStream_t stream) {
   const size_t sm = plain ? plain_smem_bytes(a.k) : fast_smem_bytes(a.k, a.ndense);
