@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-bound ablation")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
     ap.add_argument("--no-pareto", action="store_true", help="skip the heavy-tail (Pareto, k=4096) leg")
+    ap.add_argument("--no-fastsearch", action="store_true", help="skip the paper's FastSearch schedule leg")
     ap.add_argument("--no-tune", action="store_true", help="time the default tuning instead of gm_tune's")
     ap.add_argument("--tuning-file", default=None, help="load the tuning table from this file if it exists, "
                     "else tune and save it there")
@@ -561,6 +562,8 @@ def main():
         line["graph"] = graph_leg(args, timed, sketch_call, ms_main, (rp, ids, w))
     if single and not args.no_pareto:
         line["pareto_k4096"] = pareto_leg(args)
+    if single and not args.no_fastsearch:
+        line["fastsearch_k1024"] = fastsearch_leg((rp, ids, w), s_main, y_main, ms_main, st_main, n_rows)
     if single and not args.no_learned:
         line["learned_k1024"] = learned_ablation(args, timed, sketch_call, (rp, ids, w), s_main, y_main, ms_main,
                                                  st_main, n_rows)
@@ -615,6 +618,32 @@ def pareto_leg(args):
     out["speedup_vs_plain"] = out["plain"]["ms_per_step"] / out["fastgm"]["ms_per_step"]
     out["speedup_vs_no_bound"] = out["fastgm_no_bound"]["ms_per_step"] / out["fastgm"]["ms_per_step"]
     return out
+
+
+def fastsearch_leg(dev_csr, s_main, y_main, ms_main, st_main, n_rows, reps=3):
+    """The paper's own first pass on the benchmark batch (Algorithm 1: FastSearch's
+    budget rounds R = k, 2k, ... over the rows not yet filled, then FastPrune up to
+    each row's y*), against the closed-form bound of the main step; the same
+    registers, bit for bit.  The time is the sum of the rounds and FastPrune."""
+    import torch
+    from paper_2302_05176_gb300 import fastsearch
+    rp, ids, w = dev_csr
+    fastsearch.fastsearch_sketch(rp, ids, w, K_MAIN, SEED)  # warm-up
+    runs = []
+    for _ in range(reps):
+        s, y, info = fastsearch.fastsearch_sketch(rp, ids, w, K_MAIN, SEED)
+        runs.append(info)
+    ms = float(np.median([i["search_ms"] + i["prune_ms"] for i in runs]))
+    info = runs[-1]
+    return {"rounds": info["rounds"], "ms_per_step": ms, "sketches_per_s": n_rows / (ms * 1e-3),
+            "search_ms": float(np.median([i["search_ms"] for i in runs])),
+            "prune_ms": float(np.median([i["prune_ms"] for i in runs])),
+            "search_arrivals_per_sketch": info["search_arrivals"] / n_rows,
+            "prune_kept_arrivals_per_sketch": info["prune_kept"] / n_rows,
+            "closed_form_kept_arrivals_per_sketch": st_main["kept"] / n_rows,
+            "closed_form_speedup": ms / ms_main,
+            "identical_to_closed_form": bool(torch.equal(s, s_main) and
+                                             torch.equal(y.view(torch.int64), y_main.view(torch.int64)))}
 
 
 def graph_leg(args, timed, sketch_call, ms_main, dev_csr):
