@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop leg")
     ap.add_argument("--no-pareto", action="store_true", help="skip the heavy-tail (Pareto, k=4096) leg")
     ap.add_argument("--no-fastsearch", action="store_true", help="skip the paper's FastSearch schedule leg")
+    ap.add_argument("--no-stream", action="store_true", help="skip the Stream-FastGM leg")
     ap.add_argument("--no-tune", action="store_true", help="time the default tuning instead of gm_tune's")
     ap.add_argument("--tuning-file", default=None, help="load the tuning table from this file if it exists, "
                     "else tune and save it there")
@@ -564,6 +565,8 @@ def main():
         line["pareto_k4096"] = pareto_leg(args)
     if single and not args.no_fastsearch:
         line["fastsearch_k1024"] = fastsearch_leg((rp, ids, w), s_main, y_main, ms_main, st_main, n_rows)
+    if single and not args.no_stream:
+        line["stream_k1024"] = stream_leg()
     if single and not args.no_learned:
         line["learned_k1024"] = learned_ablation(args, timed, sketch_call, (rp, ids, w), s_main, y_main, ms_main,
                                                  st_main, n_rows)
@@ -644,6 +647,42 @@ def fastsearch_leg(dev_csr, s_main, y_main, ms_main, st_main, n_rows, reps=3):
             "closed_form_speedup": ms / ms_main,
             "identical_to_closed_form": bool(torch.equal(s, s_main) and
                                              torch.equal(y.view(torch.int64), y_main.view(torch.int64)))}
+
+
+def stream_leg(n_distinct=1 << 20, n_items=1 << 23, chunk=1 << 20, k=K_MAIN, reps=3):
+    """Stream-FastGM (Algorithm 2) on the device: a stream of 8 M items drawn from
+    1 M distinct ids (each id with one Exp(1) weight, repeats uniform), ingested in
+    1 M-item chunks into one running sketch; items/s over the whole stream, and the
+    registers against gm_sketch of the distinct set."""
+    import torch
+    from paper_2302_05176_gb300 import gm
+    from paper_2302_05176_gb300 import workloads as W
+    rng = np.random.default_rng(SEED)
+    dist_ids = W._distinct_ids(rng, n_distinct, W.ID_SPACE).astype(np.int32)
+    dist_w = rng.exponential(size=n_distinct)
+    pick = rng.integers(0, n_distinct, n_items)
+    pick[:n_distinct] = rng.permutation(n_distinct)  # every distinct id occurs
+    rng.shuffle(pick)
+    ids = torch.from_numpy(dist_ids[pick]).cuda()
+    w = torch.from_numpy(dist_w[pick]).cuda()
+    chunks = [(ids[i:i + chunk], w[i:i + chunk]) for i in range(0, n_items, chunk)]
+    times = []
+    for _ in range(reps + 1):
+        sk = gm.StreamSketch(k, SEED)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for ci, cw in chunks:
+            sk.ingest(ci, cw)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times[1:]))
+    rp = torch.tensor([0, n_distinct], dtype=torch.int64, device="cuda")
+    s0, y0, _ = gm.gm_sketch(rp, torch.from_numpy(dist_ids).cuda(), torch.from_numpy(dist_w).cuda(), k, SEED)
+    same = bool(torch.equal(sk.s, s0[0]) and torch.equal(sk.y.view(torch.int64), y0[0].view(torch.int64)))
+    return {"items": n_items, "distinct": n_distinct, "chunk": chunk, "k": k, "ms": ms,
+            "items_per_s": n_items / (ms * 1e-3), "identical_to_distinct_set_sketch": same}
 
 
 def graph_leg(args, timed, sketch_call, ms_main, dev_csr):
