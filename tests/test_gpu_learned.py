@@ -204,6 +204,27 @@ def test_learned_bound_against_features_and_oracle(k):
     assert np.allclose(got, np.exp(pred + margin), rtol=3e-4), np.abs(got / np.exp(pred + margin) - 1).max()
 
 
+def test_learned_bound_overlapping_rows_stay_in_bounds():
+    """Row offsets that do not ascend make rows overlap, so the long rows' pieces
+    can outnumber the lists sized from nnz: such a row gets t = -1 (no learned
+    bound, the closed form) and every other row its usual bound."""
+    rng = np.random.default_rng(12)
+    n = 100_000
+    ids = torch.from_numpy(rng.choice(1 << 24, n, replace=False).astype(np.int32)).cuda()
+    w = torch.from_numpy(rng.exponential(size=n)).cuda()
+    params = gm.gm_model_init(5)
+    full = torch.tensor([0, n], dtype=torch.int64, device="cuda")
+    t_full = float(gm.gm_learned_bound(full, w, 256, params, 0.0)[0])
+    rp = torch.tensor([0, n] * 10 + [0], dtype=torch.int64, device="cuda")  # rows 0, 2, ... span everything
+    t = gm.gm_learned_bound(rp, w, 256, params, 0.0).cpu().numpy()
+    full_rows, empty_rows = t[0::2], t[1::2]
+    assert np.all((full_rows == -1.0) | (full_rows == t_full)), full_rows
+    assert (full_rows == -1.0).any() and (full_rows == t_full).any()
+    empty = torch.tensor([0, 0], dtype=torch.int64, device="cuda")
+    t_empty = float(gm.gm_learned_bound(empty, w[:0], 256, params, 0.0)[0])
+    assert np.all(empty_rows == t_empty)
+
+
 def test_learned_bound_of_every_row_length():
     """Rows at the warp and piece limits (2,048 elements, and multiples of it) and long rows
     (their features gathered piece by piece over the grid) get the bound
