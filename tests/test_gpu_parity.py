@@ -112,6 +112,29 @@ def test_long_rows_split_into_chunks(tight):
         assert outs["fastgm"][2]["rows_escalated"] >= 0
 
 
+@pytest.mark.parametrize("tight", [0, gm.GM_FLAG_TIGHT_BOUND])
+def test_wide_shape_long_rows_and_escalations(tight):
+    """k = 4096 runs 1024-thread CTAs: long rows cut into chunks merged across CTAs
+    and, with a shrunken bound, rows redone by the escalation kernel.  The registers
+    equal the plain sketch's and the 512-thread shape's (the all-integer arithmetic
+    runs there), bit for bit."""
+    rng = np.random.default_rng(23)
+    rows = []
+    for n in [70_000, 33_000, 5, 40_000, 1200] + [int(x) for x in rng.integers(1, 3000, 40)]:
+        ids = np.sort(rng.choice(1 << 24, size=n, replace=False)).astype(np.int32)
+        rows.append((ids, W.pareto_weights(rng, n, 1.2, 1e-3) if n > 2000 else rng.standard_exponential(n)))
+    X = W.from_rows(rows)
+    k = 4096
+    f = gm.GM_FLAG_VALIDATE | tight
+    s0, y0, st0 = run(gm.gm_sketch, X, k, 31, flags=f)
+    s1, y1, _ = run(gm.gm_sketch, X, k, 31, flags=f | gm.GM_FLAG_INT_PRODUCTS)
+    s2, y2, _ = run(gm.gm_sketch_plain, X, k, 31)
+    for s, y in ((s1, y1), (s2, y2)):
+        assert np.array_equal(s0, s) and np.array_equal(y0.view(np.int64), y.view(np.int64))
+    if tight:
+        assert st0["rows_escalated"] > 0
+
+
 def test_bound_modes_agree():
     X = W.lognormal_batch(seed=9, n_rows=16, median=400.0, hi=2000)
     k = 512
