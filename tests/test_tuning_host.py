@@ -25,7 +25,7 @@ def test_defaults_and_keys():
 
 
 @pytest.mark.parametrize("bad", [{"p_first": 0.0}, {"p_first": 1.0}, {"light_max": 0.0},
-                                 {"light_max": 50.0}, {"medium_max": 300.0}, {"heavy_max": float("inf")}])
+                                 {"light_max": 70.0}, {"medium_max": 300.0}, {"heavy_max": float("inf")}])
 def test_invalid_tunings_are_refused(bad):
     with pytest.raises(gm.GmError):
         gm.tuning_set(64, 100, **bad)
