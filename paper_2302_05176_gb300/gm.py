@@ -28,12 +28,15 @@ GM_MODEL_PARAMS = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
 
 
 class GmError(RuntimeError):
+    """A non-zero status of a libgm call: .code (GM_E*) and the call's name."""
+
     def __init__(self, code, what):
         super().__init__("%s: %s (code %d)" % (what, strerror(code) if _lib else "libgm", code))
         self.code = code
 
 
 class gm_stats(ctypes.Structure):
+    """gm_stats of include/gm.h: the status and work counters of one call."""
     _fields_ = [("arrivals", ctypes.c_uint64), ("elements", ctypes.c_uint64), ("screened_out", ctypes.c_uint64),
                 ("heavy_elements", ctypes.c_uint64), ("rows_escalated", ctypes.c_uint64),
                 ("cas_retries", ctypes.c_uint64), ("cycles_light", ctypes.c_uint64),
@@ -49,6 +52,7 @@ class gm_stats(ctypes.Structure):
 
 
 class gm_tuning(ctypes.Structure):
+    """gm_tuning of include/gm.h: first-pass quantile and routing thresholds."""
     _fields_ = [("p_first", ctypes.c_float), ("light_max", ctypes.c_float), ("medium_max", ctypes.c_float),
                 ("heavy_max", ctypes.c_float)]
 
@@ -134,10 +138,12 @@ def lib():
 
 
 def strerror(code):
+    """The message of a libgm status code."""
     return lib().gm_strerror(int(code)).decode()
 
 
 def version():
+    """libgm's version string."""
     return lib().gm_version().decode()
 
 
@@ -161,6 +167,7 @@ def _check(rc, what):
 
 
 def sketch_workspace_bytes(n_rows, nnz, k, flags=0):
+    """Device workspace bytes gm_sketch / gm_sketch_plain need for this batch shape."""
     n = lib().gm_sketch_workspace_bytes(int(n_rows), int(nnz), int(k), int(flags))
     if n == 0:
         raise GmError(GM_EINVAL, "gm_sketch_workspace_bytes")
@@ -168,6 +175,7 @@ def sketch_workspace_bytes(n_rows, nnz, k, flags=0):
 
 
 def workspace(n_rows, nnz, k, flags=0, device=None):
+    """A device workspace (uint8 tensor) for gm_sketch on this batch shape."""
     return torch.empty(sketch_workspace_bytes(n_rows, nnz, k, flags), dtype=torch.uint8,
                        device=device or torch.device("cuda"))
 
@@ -216,6 +224,7 @@ def gm_status(ws, stream=None):
 
 
 def gm_jaccard(s_a, s_b, out=None, stream=None):
+    """Per pair, the fraction of registers holding the same element (Sec. 1): float64 [n_pairs]."""
     _need_cuda(s_a, torch.int32, "s_a")
     _need_cuda(s_b, torch.int32, "s_b")
     if s_a.shape != s_b.shape or s_a.dim() != 2:
@@ -228,6 +237,7 @@ def gm_jaccard(s_a, s_b, out=None, stream=None):
 
 
 def gm_cardinality(y, out=None, stream=None):
+    """Per row, (k - 1) / sum_j y_j (Sec. 2.4): float64 [n_rows]; 0 when a register is unfilled."""
     _need_cuda(y, torch.float64, "y")
     n, k = y.shape
     if out is None:
@@ -237,6 +247,7 @@ def gm_cardinality(y, out=None, stream=None):
 
 
 def gm_merge(s_a, y_a, s_b, y_b, s_out=None, y_out=None, stream=None):
+    """The sketch of the union (Sec. 2.3): per register the smaller (y, id)."""
     for t, d, nm in ((s_a, torch.int32, "s_a"), (s_b, torch.int32, "s_b"), (y_a, torch.float64, "y_a"),
                      (y_b, torch.float64, "y_b")):
         _need_cuda(t, d, nm)
@@ -279,6 +290,7 @@ def gm_row_ln_ystar(y, out=None, stream=None):
 
 
 def gm_model_init(seed, params=None, device=None, stream=None):
+    """Seeded initial network parameters (float32 [GM_MODEL_PARAMS])."""
     if params is None:
         params = torch.empty(GM_MODEL_PARAMS, dtype=torch.float32, device=device or torch.device("cuda"))
     _need_cuda(params, torch.float32, "params")
@@ -288,6 +300,7 @@ def gm_model_init(seed, params=None, device=None, stream=None):
 
 
 def gm_model_forward(params, feats, out=None, stream=None):
+    """The predicted ln bound of each sample (float32 [n]) from its 8 features."""
     _need_cuda(params, torch.float32, "params")
     _need_cuda(feats, torch.float32, "feats")
     n = feats.shape[0]
@@ -299,6 +312,7 @@ def gm_model_forward(params, feats, out=None, stream=None):
 
 
 def gm_model_grad_workspace_bytes():
+    """Device workspace bytes of gm_model_grad."""
     return int(lib().gm_model_grad_workspace_bytes())
 
 
@@ -318,15 +332,18 @@ def gm_model_grad(params, feats, target, tau, grad=None, loss=None, ws=None, str
 
 
 def gm_model_adam(params, adam, grad, lr, step, stream=None):
+    """One Adam step on the parameters in place; `adam` holds the moments (updated too)."""
     _check(lib().gm_model_adam(_ptr(params), _ptr(adam), _ptr(grad), float(lr), int(step), _stream_handle(stream)),
            "gm_model_adam")
 
 
 def gm_model_save(params, path, stream=None):
+    """Write the parameters to a file (header with magic and shape)."""
     _check(lib().gm_model_save(_ptr(params), os.fsencode(path), _stream_handle(stream)), "gm_model_save")
 
 
 def gm_model_load(path, params=None, device=None, stream=None):
+    """Read parameters written by gm_model_save into params."""
     if params is None:
         params = torch.empty(GM_MODEL_PARAMS, dtype=torch.float32, device=device or torch.device("cuda"))
     _check(lib().gm_model_load(_ptr(params), os.fsencode(path), _stream_handle(stream)), "gm_model_load")
@@ -350,6 +367,7 @@ def gm_learned_bound(row_ptr, w, k, params, margin=0.0, out=None, ws=None, strea
 
 
 def sketch_learned_workspace_bytes(n_rows, nnz, k):
+    """Device workspace bytes of gm_sketch_learned for this batch shape."""
     n = lib().gm_sketch_learned_workspace_bytes(int(n_rows), int(nnz), int(k))
     if n == 0:
         raise GmError(GM_EINVAL, "gm_sketch_learned_workspace_bytes")
@@ -417,6 +435,7 @@ class SketchGraph:
 # --- autotuning (gm_tune / gm_tuning_*) -------------------------------------------------------
 
 def tuning_default():
+    """The compiled default tuning as a dict."""
     t = gm_tuning()
     lib().gm_tuning_default(ctypes.byref(t))
     return t.as_dict()
@@ -446,6 +465,7 @@ def gm_tune(row_ptr, ids, w, k, seed, flags=0, s_out=None, y_out=None, ws=None, 
 
 
 def tuning_set(k, mean_row_len, **values):
+    """Install a tuning for (k, mean row length) in the process-wide table."""
     _check(lib().gm_tuning_set(int(k), int(mean_row_len), ctypes.byref(_tuning(values))), "gm_tuning_set")
 
 
@@ -456,14 +476,17 @@ def tuning_get(k, mean_row_len):
 
 
 def tuning_clear():
+    """Empty the process-wide tuning table."""
     lib().gm_tuning_clear()
 
 
 def tuning_save(path):
+    """Write the tuning table as text."""
     _check(lib().gm_tuning_save(os.fsencode(path)), "gm_tuning_save")
 
 
 def tuning_load(path):
+    """Read a tuning table written by tuning_save (entries are added)."""
     _check(lib().gm_tuning_load(os.fsencode(path)), "gm_tuning_load")
 
 
@@ -516,6 +539,7 @@ def gm_sketch_bounded(row_ptr, ids, w, k, seed, bound_row, flags=0, s_out=None, 
 
 
 def gm_row_ystar(y, out=None, stream=None):
+    """Per row, the largest register y* (float64 [n_rows]; +inf if one is unfilled)."""
     _need_cuda(y, torch.float64, "y")
     n, k = y.shape
     out = torch.empty(n, dtype=torch.float64, device=y.device) if out is None else out
