@@ -62,3 +62,33 @@ def test_argument_errors_before_launch(libgm):
     assert sk(fake, fake, fake, -1, 10, 8, 1, 0, fake, fake, fake, 1 << 20, None) == 1     # n_rows < 0
     assert sk(fake, fake, fake, 1, 10, 8, 1, 0, fake, fake, None, 1 << 20, None) == 1      # no workspace
     assert sk(fake, fake, fake, 1, 10, 8, 1, 0, fake, fake, fake, 16, None) == 2           # too small
+    assert sk(fake, fake, fake, 1, 10, 8, 1, 0, fake, fake, vp(0x1010), 1 << 20, None) == 1  # workspace off 256 B
+
+
+def test_host_side_workspace_sizes(libgm):
+    """The host pipeline's workspace follows its largest chunk of rows; the learned
+    pre-pass's grows with the batch; invalid shapes give 0 (host-only queries)."""
+    import numpy as np
+    vp = ctypes.c_void_p
+    loose = libgm.gm_sketch_host_workspace_bytes
+    loose.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
+    loose.restype = ctypes.c_size_t
+    tight = libgm.gm_sketch_host_workspace_bytes_csr
+    tight.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    tight.restype = ctypes.c_size_t
+    lens = np.where(np.arange(4000) < 100, 1000, 1)
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    p = rp.ctypes.data_as(vp)
+    t, l = tight(p, 4000, 256), loose(4000, int(rp[-1]), 256)
+    assert 0 < t < l
+    even = np.arange(4001, dtype=np.int64) * 26  # the same elements spread evenly: smaller chunks
+    assert tight(even.ctypes.data_as(vp), 4000, 256) < t
+    bad = rp.copy()
+    bad[10], bad[11] = bad[11], bad[10]  # decreasing
+    assert tight(bad.ctypes.data_as(vp), 4000, 256) == 0
+    assert tight(p, 4000, 0) == 0 and loose(4000, int(rp[-1]), 1 << 20) == 0
+    lb = libgm.gm_learned_bound_workspace_bytes
+    lb.argtypes = [ctypes.c_int32, ctypes.c_int64]
+    lb.restype = ctypes.c_size_t
+    assert 0 < lb(10, 1000) < lb(10, 1_000_000) and lb(10, 1000) < lb(100_000, 1000)
+    assert lb(-1, 10) == 0 and lb(10, -1) == 0
