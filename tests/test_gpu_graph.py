@@ -15,7 +15,7 @@ def same(a, b):
     return torch.equal(a[0], b[0]) and torch.equal(a[1].view(torch.int64), b[1].view(torch.int64))
 
 
-@pytest.mark.parametrize("k", [64, 1024])
+@pytest.mark.parametrize("k", [64, 1024, 4096])  # 4096: the 1024-thread CTA shape
 def test_graph_replay_equals_direct_call(k):
     X = W.lognormal_batch(seed=12, n_rows=96, median=900.0)
     rp, ids, w = gm.to_device(X)
