@@ -13,7 +13,8 @@ from paper_2302_05176_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n_rows,k,pinned", [(300, 64, False), (3000, 256, True), (5000, 1024, True)])
+@pytest.mark.parametrize("n_rows,k,pinned", [(300, 64, False), (3000, 256, True), (5000, 1024, True),
+                                              (600, 4096, True)])
 def test_host_pipeline_equals_device_call(n_rows, k, pinned):
     X = W.lognormal_batch(seed=n_rows, n_rows=n_rows, median=400.0)
     X.w[X.row_ptr[7]:X.row_ptr[8]] = 0.0  # a row without positive weights

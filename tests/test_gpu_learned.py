@@ -152,7 +152,7 @@ def long_batch():
     return W.from_rows(rows)
 
 
-@pytest.mark.parametrize("k", [64, 1024])
+@pytest.mark.parametrize("k", [64, 1024, 4096])
 def test_learned_sketch_exact_for_any_model(k):
     X = long_batch()
     rp, ids, w = gm.to_device(X)
