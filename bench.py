@@ -41,8 +41,9 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU-oracle sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "fastgm"],
-                    help="fastgm: time only the FastGM step (the case profiled with ncu)")
+    ap.add_argument("--only", default="all", choices=["all", "fastgm", "prepass"],
+                    help="fastgm: time only the FastGM step (the case profiled with ncu); prepass: only the "
+                         "learned bound's pre-pass (gm_learned_bound) at the seeded initial parameters")
     ap.add_argument("--k", type=int, default=K_MAIN, help="k of the --only fastgm step")
     ap.add_argument("--flags", type=int, default=0, help="gm_sketch flags of the --only fastgm step")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-bound ablation")
@@ -477,6 +478,19 @@ def main():
 
     def sketch_call(fn, k, flags=0):
         return lambda s_out, y_out, ws: fn(rp, ids, w, k, SEED, flags=flags, s_out=s_out, y_out=y_out, ws=ws)
+
+    if args.only == "prepass":
+        params = gm.gm_model_init(3)
+        t_out = torch.empty(n_rows, dtype=torch.float32, device="cuda")
+        lb_ws = torch.empty(L.gm_learned_bound_workspace_bytes(n_rows, nnz), dtype=torch.uint8, device="cuda")
+        call = lambda: gm.gm_learned_bound(rp, w, args.k, params, 0.0, out=t_out, ws=lb_ws)
+        for _ in range(max(3, args.warmup)):
+            call()
+        ms = _time_ms_cold(call, reps=args.steps)
+        if rank == 0:
+            print(json.dumps({"only": "prepass k=%d" % args.k, "ms": ms,
+                              "gbs": (8 * nnz + 12 * n_rows + 8) / (ms * 1e-3) / 1e9}), flush=True)
+        return
 
     # autotuned stream shapes and first-pass quantile per (k, row-length bucket), untimed;
     # --tuning-file reuses a saved table (so that a profiled run times the same tuning)
