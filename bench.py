@@ -756,7 +756,8 @@ def serving_leg(args):
     """Replay a Poisson stream of sketch / Jaccard / cardinality requests (20k req/s,
     n+ log-uniform in [100, 5e6], Exp(1) / Pareto(1.5) weights, k in {256, 1024,
     4096}) against the serving engine.  Each request is submitted at its arrival
-    time; its latency runs from that time to the engine's completion stamp."""
+    time; its latency runs from that time to the engine's completion stamp.  Then
+    the same requests all at once (`burst`): the engine's capacity."""
     import torch
     from paper_2302_05176_gb300 import server as S
     from paper_2302_05176_gb300 import workloads as W
@@ -771,10 +772,15 @@ def serving_leg(args):
     out["p50_ms_of_runs"] = [r["p50_ms"] for r in runs]
     out["p99_ms_of_runs"] = [r["p99_ms"] for r in runs]
     out["generate_s"] = gen_s
+    b = _serve_once(args, reqs, bufs, burst=True)
+    out["burst"] = {key: b[key] for key in ("span_s", "throughput_rps", "elements_per_s", "p50_ms", "p99_ms",
+                                            "sketch_batches", "mean_batch_rows")}
     return out
 
 
-def _serve_once(args, reqs, bufs):
+def _serve_once(args, reqs, bufs, burst=False):
+    """One replay of the request stream; burst=True submits every request at once
+    (the engine's capacity: throughput with the queue always full)."""
     from paper_2302_05176_gb300 import server as S
     with S.Server(seed=SEED, device_bytes=16 << 30, n_streams=args.serve_streams, flags=args.serve_flags,
                   stage_pinned=args.serve_stage_pinned) as srv:
@@ -788,7 +794,7 @@ def _serve_once(args, reqs, bufs):
         tick, due = {}, {}
         start = S.now_ns() + 1_000_000
         for i, r in enumerate(reqs):
-            d = start + int(r.t_arrive * 1e9)
+            d = start if burst else start + int(r.t_arrive * 1e9)
             while S.now_ns() < d:
                 pass
             if r.kind == "sketch":
@@ -816,7 +822,7 @@ def _serve_once(args, reqs, bufs):
     pct = lambda v, q: float(np.percentile(v, q)) if len(v) else None
     return {"requests": len(reqs), "sketches": len(lat["sketch"]),
             "queries": len(lat["jaccard"]) + len(lat["cardinality"]),
-            "offered_rate_rps": SERVE_RATE, "span_s": span, "throughput_rps": len(reqs) / span,
+            "offered_rate_rps": None if burst else SERVE_RATE, "span_s": span, "throughput_rps": len(reqs) / span,
             "elements_per_s": nnz / span, "elements": nnz,
             "p50_ms": pct(every, 50), "p99_ms": pct(every, 99),
             "sketch_p50_ms": pct(lat["sketch"], 50), "sketch_p99_ms": pct(lat["sketch"], 99),
