@@ -27,8 +27,11 @@ __host__ __device__ inline size_t fast_area_bytes() {
   size_t m = maps > hashes ? maps : hashes;
   return m > med ? m : med;
 }
+// Per-warp screening buffer of the light path: the survivors of a 32-element
+// screening batch with their 1/v and id (doubles first: 8-byte aligned).
+constexpr size_t WBUF_BYTES = 32 * 8 + 32 * 4 + 32 * 4;
 __host__ __device__ inline size_t fast_smem_bytes(int k, int ndense) {
-  return (size_t)k * sizeof(Reg) + fast_area_bytes() + (size_t)ndense * pi_stride(k) * 2 + (size_t)WARPS * 32 * 4;
+  return (size_t)k * sizeof(Reg) + fast_area_bytes() + (size_t)ndense * pi_stride(k) * 2 + (size_t)WARPS * WBUF_BYTES;
 }
 // The plain kernel: registers | one dense permutation per warp.
 __host__ __device__ inline size_t plain_smem_bytes(int k) {
@@ -42,9 +45,12 @@ __host__ __device__ inline size_t plain_smem_bytes(int k) {
 // --------------------------------------------------------------------------
 template <int ARITH>
 __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int n, uint64_t Tbits, float Tf,
-                                            Reg* regs, uint32_t* map, uint32_t* wbuf, SmemScalars& sh,
+                                            Reg* regs, uint32_t* map, unsigned char* wbuf, SmemScalars& sh,
                                             Counters& cnt, bool& gave_up) {
   const int tid = threadIdx.x, lane = tid & 31;
+  double* wb_r = reinterpret_cast<double*>(wbuf);            // 1/v of each survivor
+  uint32_t* wb_slot = reinterpret_cast<uint32_t*>(wbuf + 256);  // its slot in the unit
+  int32_t* wb_id = reinterpret_cast<int32_t*>(wbuf + 384);     // its id
   const int k = a.k;
   const float kf = (float)k;
   int e = -1, z = 0, msize = 0;
@@ -67,8 +73,10 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
         }
         const int slot = base + lane;
         bool surv = false;
+        double v = 0.0;
+        int32_t idv = 0;
         if (slot < n) {
-          const double v = a.w[lo + slot];
+          v = a.w[lo + slot];
           if (positive_finite(v)) {
             ++cnt.elements;
             const float vf = f32_trunc(v);
@@ -77,7 +85,8 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
               const uint32_t tag = lam > a.heavy_max ? TAG_SUPER : (lam > a.medium_max ? TAG_HEAVY : TAG_MEDIUM);
               a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | tag;
             } else {
-              const Words wd = philox((uint32_t)a.ids[lo + slot], 0u, a.key0, a.key1);
+              idv = a.ids[lo + slot];
+              const Words wd = philox((uint32_t)idv, 0u, a.key0, a.key1);
               if (screen_out(wd.w1, vf, Tf, kf))
                 ++cnt.screened;  // first arrival certainly above T: nothing of it counts
               else
@@ -86,7 +95,12 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
           }
         }
         const uint32_t sm = __ballot_sync(FULL, surv);
-        if (surv) wbuf[__popc(sm & lanemask_lt())] = (uint32_t)slot;
+        if (surv) {  // one reciprocal per screening batch, not one per lane refill
+          const int p = __popc(sm & lanemask_lt());
+          wb_r[p] = arr_rcp<ARITH>(v);
+          wb_slot[p] = (uint32_t)slot;
+          wb_id[p] = idv;
+        }
         wcount = __popc(sm);
         __syncwarp();
         continue;
@@ -94,10 +108,10 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
       const int take = min(__popc(nmask), wcount);
       const int rank = __popc(nmask & lanemask_lt());
       if (e < 0 && rank < take) {
-        e = (int)wbuf[wcount - 1 - rank];
-        const int64_t g = lo + e;
-        id = a.ids[g];
-        R = arr_rcp<ARITH>(a.w[g]);
+        const int q = wcount - 1 - rank;
+        e = (int)wb_slot[q];
+        id = wb_id[q];
+        R = wb_r[q];
         z = 0;
         acc = fix_zero();
         msize = 0;
@@ -272,7 +286,7 @@ __device__ __forceinline__ void flush_counters(const SketchArgs& a, Counters& cn
 // bound from `first_pass` on, until every register is filled.
 template <int ARITH>
 __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t lo, int n, int first_pass, Reg* regs,
-                                           uint32_t* area, uint16_t* dense, uint32_t* wbuf, SmemScalars& sh,
+                                           uint32_t* area, uint16_t* dense, unsigned char* wbuf, SmemScalars& sh,
                                            Counters& cnt, bool& gave_up) {
   const int tid = threadIdx.x;
   float sumv;
@@ -298,7 +312,7 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
     reset_lists(sh);
     __syncthreads();
     clk_add(cnt, CLK_SETUP, t);
-    light_phase<ARITH>(a, lo, n, Tbits, Tf, regs, area, wbuf + (tid >> 5) * 32, sh, cnt, gave_up);
+    light_phase<ARITH>(a, lo, n, Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt, gave_up);
     clk_add(cnt, CLK_LIGHT, t);
     __syncthreads();
     clk_add(cnt, CLK_WAIT, t);
@@ -352,8 +366,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
   Reg* regs = reinterpret_cast<Reg*>(smem);
   uint32_t* area = reinterpret_cast<uint32_t*>(smem + (size_t)k * sizeof(Reg));
   uint16_t* dense = reinterpret_cast<uint16_t*>(smem + (size_t)k * sizeof(Reg) + fast_area_bytes());
-  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem + (size_t)k * sizeof(Reg) + fast_area_bytes() +
-                                               (size_t)a.ndense * pi_stride(k) * 2);
+  unsigned char* wbuf = smem + (size_t)k * sizeof(Reg) + fast_area_bytes() + (size_t)a.ndense * pi_stride(k) * 2;
   const int tid = threadIdx.x;
   Counters cnt;
   cnt.zero();
@@ -397,7 +410,8 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
       reset_lists(sh);
       __syncthreads();
       long long t = read_clock();
-      light_phase<ARITH>(a, clo, (int)(chi - clo), Tbits, Tf, regs, area, wbuf + (tid >> 5) * 32, sh, cnt, gave_up);
+      light_phase<ARITH>(a, clo, (int)(chi - clo), Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt,
+                         gave_up);
       clk_add(cnt, CLK_LIGHT, t);
       __syncthreads();
       clk_add(cnt, CLK_WAIT, t);
