@@ -11,7 +11,7 @@ constexpr int CTAS_PER_SM = 1024 / BLOCK;
 constexpr int MAPCAP = GM_MAPCAP;  // displaced positions a light lane can track
 
 struct SmemScalars {
-  int pool, hcount, pcount, c_med, c_heavy, c_pheavy, c_super, c_psuper, unit, last;
+  int pool, hcount, bcount, pcount, c_med, c_heavy, c_pheavy, c_super, c_psuper, unit, last;
   float red_f[WARPS];
   int red_i[WARPS];
   double red_d[WARPS];
@@ -82,8 +82,13 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
             const float vf = f32_trunc(v);
             const float lam = kf * (1.0f - __expf(-(vf * Tf)));  // expected arrivals <= T (routing only)
             if (lam > a.light_max) {
-              const uint32_t tag = lam > a.heavy_max ? TAG_SUPER : (lam > a.medium_max ? TAG_HEAVY : TAG_MEDIUM);
-              a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | tag;
+              // 8-lane work from the front of the unit's list, 32-lane and dense work from
+              // its back: each warp phase scans only its own class
+              if (lam > a.medium_max)
+                a.list[lo + n - 1 - atomicAdd(&sh.bcount, 1)] =
+                    (uint32_t)slot | (lam > a.heavy_max ? TAG_SUPER : TAG_HEAVY);
+              else
+                a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | TAG_MEDIUM;
             } else {
               idv = a.ids[lo + slot];
               const Words wd = philox((uint32_t)idv, 0u, a.key0, a.key1);
@@ -188,11 +193,12 @@ __device__ __forceinline__ void clk_add(Counters&, int which, long long& t) {
 // permutations (warps < ndense).  (Lowering T to the running y* at the barriers
 // saved 2 % of the arrivals and cost more in barriers: measured and dropped.)
 template <int ARITH>
-__device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uint64_t Tbits, Reg* regs,
+__device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, int n, uint64_t Tbits, Reg* regs,
                                             uint32_t* area, uint16_t* dense, SmemScalars& sh, Counters& cnt,
                                             bool& gave_up, long long& t) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nh = sh.hcount;
+  const int nh = sh.hcount, nb = sh.bcount;
+  uint32_t* back = a.list + lo + n - nb;  // the 32-lane and dense entries
   {
     const int seg = lane / MED_SW;
     const HashPiN<MED_SLOTS> hp{area + (warp * (32 / MED_SW) + seg) * MED_SLOTS};
@@ -203,8 +209,8 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uin
   // a warp's hash region is the same in both phases: the heavy list needs no barrier
   {
     const HashPi hp{area + warp * HASH_SLOTS};
-    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_heavy, TAG_HEAVY, hp, HASH_MAX_FILL, nullptr,
-                         nullptr, cnt, gave_up);
+    seg_phase<ARITH, 32>(a, lo, Tbits, regs, back, nb, &sh.c_heavy, TAG_HEAVY, hp, HASH_MAX_FILL, nullptr, nullptr,
+                         cnt, gave_up);
   }
   clk_add(cnt, CLK_HEAVY, t);
   __syncthreads();  // every promotion is listed
@@ -223,8 +229,8 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, uin
     uint16_t* mine = warp < a.ndense ? dense + (size_t)warp * pi_stride(a.k)
                                      : reinterpret_cast<uint16_t*>(area) + (size_t)(warp - a.ndense) * pi_stride(a.k);
     const DensePi dp{mine};
-    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_super, TAG_SUPER, dp, 1 << 30, nullptr,
-                         nullptr, cnt, gave_up);
+    seg_phase<ARITH, 32>(a, lo, Tbits, regs, back, nb, &sh.c_super, TAG_SUPER, dp, 1 << 30, nullptr, nullptr, cnt,
+                         gave_up);
     seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_psuper, TAG_SUPER, dp, 1 << 30,
                          nullptr, nullptr, cnt, gave_up);
   }
@@ -237,6 +243,7 @@ __device__ __forceinline__ void reset_lists(SmemScalars& sh) {
   if (threadIdx.x == 0) {
     sh.pool = 0;
     sh.hcount = 0;
+    sh.bcount = 0;
     sh.pcount = 0;
     sh.c_med = sh.c_heavy = sh.c_pheavy = sh.c_super = sh.c_psuper = 0;
   }
@@ -316,7 +323,7 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
     clk_add(cnt, CLK_LIGHT, t);
     __syncthreads();
     clk_add(cnt, CLK_WAIT, t);
-    warp_phases<ARITH>(a, lo, Tbits, regs, area, dense, sh, cnt, gave_up, t);
+    warp_phases<ARITH>(a, lo, n, Tbits, regs, area, dense, sh, cnt, gave_up, t);
     // a register above T may still be lowered by an arrival above T: redo wider.
     // (Without a starting sketch that is exactly an unfilled register.)
     int empty = 0;
@@ -415,7 +422,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
       clk_add(cnt, CLK_LIGHT, t);
       __syncthreads();
       clk_add(cnt, CLK_WAIT, t);
-      warp_phases<ARITH>(a, clo, Tbits, regs, area, dense, sh, cnt, gave_up, t);
+      warp_phases<ARITH>(a, clo, (int)(chi - clo), Tbits, regs, area, dense, sh, cnt, gave_up, t);
       Reg* g = a.long_regs + (int64_t)longi * k;
       for (int j = tid; j < k; j += BLOCK) {
         const Reg r = regs[j];
