@@ -300,7 +300,7 @@ int gm_sketch_learned(const int64_t* row_ptr, const int32_t* ids, const double* 
  * their expected number of arrivals below the bound -- one lane each up to
  * light_max, 8-lane segments up to medium_max, 32-lane warps up to heavy_max,
  * a dense permutation beyond.  gm_sketch takes them from a process-wide table
- * keyed by (k, floor(log2(mean row length))), else the defaults (0.05, 8, 64,
+ * keyed by (k, floor(log2(mean row length))), else the defaults (0.05, 4, 64,
  * 256).  gm_tune times candidate values on the caller's batch (coordinate
  * descent, up to two sweeps, each candidate the fastest of three timed calls
  * after one warm-up and adopted when 1 % faster; it synchronises `stream`),

@@ -60,10 +60,10 @@ namespace gm {
 // Default routing by the expected number of arrivals below T (gm_tuning): light
 // lanes up to LIGHT_MAX, 8-lane segments up to MEDIUM_MAX, 32-lane warps up to
 // HEAVY_MAX, dense permutations beyond; first-pass bound at quantile 1 - P_FIRST.
-// The values: the best of a grid over the 4,096-row lognormal batch (light 4 ..
-// 24, medium 32 .. 128, heavy 256 / 512): 2.85 ms at k = 1024 and 9.79 ms at
-// k = 4096, against 2.91 / 9.84 ms with light 6, medium 48.
-constexpr float LIGHT_MAX = 8.0f;
+// The values: the best of a grid over the 4,096-row lognormal batch (light 2 ..
+// 8, medium 32 .. 128, heavy 128 .. 512): 2.56 ms at k = 1024 and 8.58 ms at
+// k = 4096, against 2.62 / 8.80 ms with light 8.
+constexpr float LIGHT_MAX = 4.0f;
 constexpr float MEDIUM_MAX = 64.0f;
 constexpr float HEAVY_MAX = 256.0f;
 constexpr float P_FIRST = 0.05f;

@@ -15,7 +15,7 @@ def teardown_function():
 
 def test_defaults_and_keys():
     d = gm.tuning_default()
-    assert d == pytest.approx({"p_first": 0.05, "light_max": 8.0, "medium_max": 64.0, "heavy_max": 256.0})
+    assert d == pytest.approx({"p_first": 0.05, "light_max": 4.0, "medium_max": 64.0, "heavy_max": 256.0})
     assert gm.tuning_get(1024, 3000) is None
     gm.tuning_set(1024, 3000, p_first=0.1, light_max=4, medium_max=32, heavy_max=512)
     # same bucket: floor(log2 3000) = floor(log2 2048) = 11; not 4095 -> 11 too, 4096 -> 12
