@@ -39,7 +39,6 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=2)
-    ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU-oracle sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", default="all", choices=["all", "fastgm", "prepass"],
                     help="fastgm: time only the FastGM step (the case profiled with ncu); prepass: only the "
@@ -301,27 +300,106 @@ def algorithmic_bytes(nnz, n_rows, k):
     return 12 * nnz + 12 * n_rows * k
 
 
-def cpu_baseline(X, k, seed, rows_budget_s=15.0, n_rows=0):
-    """The oracle (unpruned full stream, plain C, one row per call on a thread pool) on a
-    bounded random sample of the batch's rows; throughput scaled to sketches/s."""
+CPU_SAMPLE_ROWS = 128  # rows of the batch the oracle sketches per CPU measurement (both arms)
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline lines."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_sample_rows(X, n_rows=CPU_SAMPLE_ROWS):
+    """The fixed random sample of batch rows that every CPU-oracle measurement uses."""
+    rng = np.random.default_rng(12345)
+    return np.sort(rng.choice(X.n_rows, size=min(n_rows, X.n_rows), replace=False))
+
+
+def cpu_sample_run(X, k, seed, rows):
+    """The oracle (unpruned full stream, plain C, one row per call on a thread pool,
+    longest rows first) over the sample rows: seconds and elements."""
     import oracle
     threads = os.cpu_count() or 1
-    rng = np.random.default_rng(12345)
-    lens = np.diff(X.row_ptr)
-    if n_rows <= 0:
-        # size the sample for ~rows_budget_s at ~4e6 arrivals/s per core
-        per_row_s = float(lens.mean()) * k / 4.0e6
-        n_rows = int(max(threads, min(X.n_rows, rows_budget_s * threads / max(per_row_s, 1e-9))))
-    rows = np.sort(rng.choice(X.n_rows, size=min(n_rows, X.n_rows), replace=False))
     oracle.lib()
     t0 = time.perf_counter()
     oracle.sketch_rows_parallel(X.row_ptr, X.ids, X.w, k, seed, rows, threads=threads)
     dt = time.perf_counter() - t0
-    nnz = int(lens[rows].sum())
-    return {"value": rows.size / dt, "unit": "sketches/s", "cores": threads, "kind": "oracle",
-            "elements_per_s": nnz / dt, "seconds": dt,
-            "sample": "%d random rows of the batch (%d elements), k=%d, unpruned full stream, %d host threads" %
-                      (rows.size, nnz, k, threads)}
+    return dt, int(np.diff(X.row_ptr)[rows].sum()), threads
+
+
+def cpu_baseline(X, k, seed):
+    """The oracle timed on the host cores, as a stated baseline (never tuned):
+    the benchmark batch's row sample on all cores (the line's value, sketches/s),
+    the single vector of n+ = 1000 at k = 128 on one thread (median of 20 runs),
+    the paper's Algorithm 1 (host, one thread) on that vector and on 8 sample rows,
+    and the heavy-tail vector's cost extrapolated from a slice of one row."""
+    import oracle
+    rows = cpu_sample_rows(X)
+    dt, nnz, threads = cpu_sample_run(X, k, seed, rows)
+    out = {"value": rows.size / dt, "unit": "sketches/s", "cores": threads, "cpu_model": cpu_model(),
+           "kind": "oracle", "elements_per_s": nnz / dt, "seconds": dt,
+           "sample": "%d random rows of the batch (%d elements), k=%d, unpruned full stream, %d host threads "
+                     "(longest rows first)" % (rows.size, nnz, k, threads)}
+    # config 1: one vector, n = 10,000, n+ = 1,000, Uniform(0,1], k = 128, one thread
+    from paper_2302_05176_gb300 import workloads as W
+    V = W.single_vector(seed=1)
+    times = []
+    for _ in range(20):
+        t0 = time.perf_counter()
+        oracle.sketch(V.row_ptr, V.ids, V.w, 128, 1)
+        times.append(time.perf_counter() - t0)
+    t_alg = []
+    for _ in range(20):
+        t0 = time.perf_counter()
+        oracle.fastgm_alg1(V.ids, V.w, 128, 1)
+        t_alg.append(time.perf_counter() - t0)
+    out["single_vector_k128_one_thread"] = {
+        "oracle_ms": 1e3 * float(np.median(times)), "oracle_sketches_per_s": 1.0 / float(np.median(times)),
+        "algorithm1_ms": 1e3 * float(np.median(t_alg)), "algorithm1_sketches_per_s": 1.0 / float(np.median(t_alg)),
+        "runs": 20}
+    # the paper's Algorithm 1 on the host, one thread, on 8 rows of the batch's sample
+    sub = rows[:8]
+    t0 = time.perf_counter()
+    arr = 0
+    for r in sub:
+        lo, hi = int(X.row_ptr[r]), int(X.row_ptr[r + 1])
+        arr += oracle.fastgm_alg1(X.ids[lo:hi], X.w[lo:hi], k, seed)[2]
+    ta = time.perf_counter() - t0
+    out["algorithm1_batch_rows_one_thread"] = {
+        "rows": int(sub.size), "elements": int(np.diff(X.row_ptr)[sub].sum()), "seconds": ta,
+        "sketches_per_s": sub.size / ta, "arrivals_per_sketch": arr / sub.size}
+    # config 3: 16 x 10^6 Pareto(1.2), k = 4096 -- a 20,000-element slice of row 0 split
+    # over the host threads (each piece a row, combined by the exact min-merge),
+    # arrivals/s extrapolated to the 6.6e10 arrivals of the whole unpruned batch
+    P = W.pareto_heavy(seed=1, n_rows=1, n_pos=20_000)
+    kp = 4096
+    cuts = np.linspace(0, P.nnz, threads + 1).astype(np.int64)
+    t0 = time.perf_counter()
+    parts = oracle.sketch_rows_parallel(cuts, P.ids, P.w, kp, seed, np.arange(threads), threads=threads)
+    sm, ym = parts[0][0], parts[1][0]
+    for q in range(1, threads):
+        sm, ym = oracle.merge(sm, ym, parts[0][q], parts[1][q])
+    tp = time.perf_counter() - t0
+    rate = P.nnz * kp / tp
+    full = 16 * 1_000_000 * kp
+    out["pareto_k4096_extrapolated"] = {
+        "slice_elements": int(P.nnz), "seconds": tp, "arrivals_per_s": rate, "threads": threads,
+        "extrapolated_seconds_per_batch": full / rate, "extrapolated_sketches_per_s": 16 / (full / rate),
+        "note": "extrapolated from the slice; the full unpruned batch (6.6e10 arrivals) is not run on the host"}
+    return out
 
 
 def run_arith(args):
@@ -373,24 +451,33 @@ def run_arith(args):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle on the host cores (the paper ships no
+    library).  Each step sketches the same fixed sample of the benchmark batch's
+    rows as the cpu_baseline leg; sketches/s over that sample, and the step time
+    extrapolated to the 4,096-row batch."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     from paper_2302_05176_gb300 import workloads as W
     X = W.lognormal_batch(seed=SEED, n_rows=N_ROWS)
-    per_step = []
-    info = None
+    rows = cpu_sample_rows(X)
+    rates = []
+    nnz = threads = 0
     for i in range(args.warmup + args.steps):
-        info = cpu_baseline(X, K_MAIN, SEED, rows_budget_s=3.0)
+        dt, nnz, threads = cpu_sample_run(X, K_MAIN, SEED, rows)
         if i >= args.warmup:
-            per_step.append(info["seconds"] / info["value"] * N_ROWS)  # seconds for the whole batch
-    v = float(np.mean([N_ROWS / s for s in per_step]))
+            rates.append(rows.size / dt)
+    v = float(np.mean(rates))
+    sample = ("%d random rows of the batch (%d elements), k=%d, unpruned full stream, %d host threads "
+              "(longest rows first); ms_per_step extrapolated to the 4096-row batch" %
+              (rows.size, nnz, K_MAIN, threads))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "sketches/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(per_step)) * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": N_ROWS / v * 1e3,
+            "ms_per_step_is": "extrapolated to the 4096-row batch from the sample's rate",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": v, "unit": "sketches/s", "cores": info["cores"], "kind": "oracle",
-                             "sample": info["sample"] + "; each step extrapolated to the 4096-row batch"},
+            "cpu_baseline": {"value": v, "unit": "sketches/s", "cores": threads, "cpu_model": cpu_model(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "sketches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -587,7 +674,7 @@ def main():
     if single and not args.no_serve:
         line["serving"] = serving_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(X, K_MAIN, SEED, n_rows=args.cpu_rows)
+        line["cpu_baseline"] = cpu_baseline(X, K_MAIN, SEED)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -153,18 +153,20 @@ int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w,
  * input and output buffers.
  *
  * The scratch is one fixed device array inside libgm, sized for
- * nnz <= GM_NOALLOC_MAX_NNZ, n_rows <= GM_NOALLOC_MAX_ROWS and k <= GM_MAX_K
- * (about 6.3 MB); every GPU that loads the library holds it until the process
- * exits.  Arguments and output are those of gm_sketch (same kernels, same
- * registers), minus the workspace.
- *   - Returns GM_ENOMEM if nnz > GM_NOALLOC_MAX_NNZ or the input needs more
- *     scratch than the fixed array holds (always fits: n_rows <=
- *     GM_NOALLOC_MAX_ROWS), GM_EINVAL for GM_FLAG_VALIDATE (a device status could
- *     not be read back) and for the argument errors of gm_sketch, GM_ECUDA on a
- *     CUDA error.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current and caches it; make that
- *     first call before any stream capture.
+ * nnz <= GM_NOALLOC_MAX_NNZ, n_rows <= GM_NOALLOC_MAX_ROWS and k <= GM_MAX_K:
+ * 10,782,208 bytes (about 10.8 MB) that every GPU which loads the library holds
+ * until the process exits.  Arguments and output are those of gm_sketch (same
+ * kernels, same registers), minus the workspace.
+ *   - Returns GM_ENOMEM if nnz > GM_NOALLOC_MAX_NNZ or n_rows >
+ *     GM_NOALLOC_MAX_ROWS (checked on the host, nothing is launched), GM_EINVAL
+ *     for the argument errors of gm_sketch, GM_ECUDA on a CUDA error.
+ *   - Errors found on the device (GM_FLAG_VALIDATE's GM_EDATA, GM_ETIMEOUT) are
+ *     recorded in the array's header: read them with gm_sketch_noalloc_status
+ *     after the call, before the next call on that device overwrites them.
+ *   - Each call made outside stream capture looks up the array's device address
+ *     (cudaGetSymbolAddress, with the calling device current) and caches it per
+ *     device; a call made during capture uses that cache, so make one call on the
+ *     device before capturing one.
  *   - All calls share the one array, which keeps the last call's contents (each
  *     call first resets what must start at zero).  Calls whose work overlaps on
  *     the GPU -- on different streams, or from different host threads without
@@ -174,6 +176,13 @@ int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w,
 #define GM_NOALLOC_MAX_ROWS (1 << 16)
 int gm_sketch_noalloc(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
                       int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* stream);
+
+/* gm_sketch_noalloc_status -- gm_status for the fixed array of gm_sketch_noalloc:
+ * waits for the work queued on `stream`, copies the device status and counters
+ * of the last gm_sketch_noalloc call on the current device into *stats (host,
+ * may be NULL) and returns GM_OK, GM_EDATA, GM_ETIMEOUT or GM_ECUDA.  Allocates
+ * nothing.  (No counterpart in the paper.) */
+int gm_sketch_noalloc_status(gm_stats* stats, void* stream);
 
 /*
  * gm_status -- wait for the work queued on `stream`, then copy the device

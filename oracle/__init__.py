@@ -47,7 +47,7 @@ def lib():
         L.gmo_arrivals.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_uint64,
                                    ctypes.c_int32, _f64p, _i32p]
         L.gmo_sketch_rows.argtypes = [_i64p, _i32p, _f64p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
-                                      _i32p, _f64p, _f64p]
+                                      _i32p, _f64p, _f64p, _i32p]
         L.gmo_fastsearch_budgets.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int64, _i64p]
         L.gmo_fastgm_alg1.argtypes = [_i32p, _f64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                       ctypes.c_int32, _i32p, _f64p, _i64p, ctypes.POINTER(ctypes.c_int64),
@@ -115,45 +115,52 @@ def arrivals(elem_id, v, k, seed, n_steps=None):
     return b, c
 
 
-def sketch(row_ptr, ids, w, k, seed, want_y2=False):
-    """Unpruned sketch of CSR rows -> (s [n_rows, k] int32, y [n_rows, k] f64[, y2])."""
+def sketch(row_ptr, ids, w, k, seed, runner_up=False):
+    """Unpruned sketch of CSR rows -> (s [n_rows, k] int32, y [n_rows, k] f64); with
+    runner_up=True also (y2, s2): per register the second candidate in (time, id)
+    order over distinct elements (+inf / -1 if there is none)."""
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     ii = np.ascontiguousarray(ids, dtype=np.int32)
     ww = np.ascontiguousarray(w, dtype=np.float64)
     n_rows = rp.size - 1
     s = np.zeros((n_rows, k), dtype=np.int32)
     y = np.zeros((n_rows, k), dtype=np.float64)
-    y2 = np.zeros((n_rows, k), dtype=np.float64) if want_y2 else None
+    y2 = np.zeros((n_rows, k), dtype=np.float64) if runner_up else None
+    s2 = np.zeros((n_rows, k), dtype=np.int32) if runner_up else None
     rc = lib().gmo_sketch_rows(_p(rp, _i64p), _p(ii, _i32p), _p(ww, _f64p), n_rows, int(k), int(seed),
-                               _p(s, _i32p), _p(y, _f64p), _p(y2, _f64p) if want_y2 else None)
+                               _p(s, _i32p), _p(y, _f64p), _p(y2, _f64p) if runner_up else None,
+                               _p(s2, _i32p) if runner_up else None)
     _check(rc, "sketch")
-    return (s, y, y2) if want_y2 else (s, y)
+    return (s, y, y2, s2) if runner_up else (s, y)
 
 
-def sketch_rows_parallel(row_ptr, ids, w, k, seed, rows, threads=None, want_y2=False):
+def sketch_rows_parallel(row_ptr, ids, w, k, seed, rows, threads=None, runner_up=False):
     """Sketch the listed rows, one ctypes call per row spread over host threads.
 
     ctypes drops the GIL during each call, so this uses several cores while the
-    C oracle itself stays single-threaded.  Returns arrays indexed like ``rows``.
+    C oracle itself stays single-threaded.  Returns arrays indexed like ``rows``
+    (the longest rows are started first, so that they do not finish last).
     """
     rp = np.asarray(row_ptr, dtype=np.int64)
     rows = np.asarray(rows, dtype=np.int64)
     threads = threads or os.cpu_count() or 1
     s = np.zeros((rows.size, k), dtype=np.int32)
     y = np.zeros((rows.size, k), dtype=np.float64)
-    y2 = np.zeros((rows.size, k), dtype=np.float64) if want_y2 else None
+    y2 = np.zeros((rows.size, k), dtype=np.float64) if runner_up else None
+    s2 = np.zeros((rows.size, k), dtype=np.int32) if runner_up else None
 
     def one(q):
         r = rows[q]
         lo, hi = int(rp[r]), int(rp[r + 1])
-        out = sketch(np.array([0, hi - lo]), ids[lo:hi], w[lo:hi], k, seed, want_y2=want_y2)
+        out = sketch(np.array([0, hi - lo]), ids[lo:hi], w[lo:hi], k, seed, runner_up=runner_up)
         s[q], y[q] = out[0][0], out[1][0]
-        if want_y2:
-            y2[q] = out[2][0]
+        if runner_up:
+            y2[q], s2[q] = out[2][0], out[3][0]
 
+    order = np.argsort(-(rp[rows + 1] - rp[rows]), kind="stable")
     with _cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        list(ex.map(one, range(rows.size)))
-    return (s, y, y2) if want_y2 else (s, y)
+        list(ex.map(one, order))
+    return (s, y, y2, s2) if runner_up else (s, y)
 
 
 def fastsearch_budgets(v, R):

@@ -270,22 +270,27 @@ static int check_weight(double v) {
 }
 
 /* ---------------------------------------------------------------------------
- * The unpruned sketch of CSR rows.  y2_out (nullable) receives, per register,
- * the second-smallest candidate time over distinct elements, so that a caller
- * can tell which registers are decided by a near-tie.
+ * The unpruned sketch of CSR rows.  y2_out and s2_out (nullable) receive, per
+ * register, the runner-up: the second candidate in the register's (time, id)
+ * order over distinct elements, so that a caller can tell which registers are
+ * decided by a near-tie and which element would win it the other way
+ * (+inf / -1 when fewer than two elements reach the register).
  * Unfilled registers: y = +inf, s = -1.
  * ------------------------------------------------------------------------- */
 int gmo_sketch_rows(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
-                    int32_t k, uint64_t seed, int32_t* s_out, double* y_out, double* y2_out) {
+                    int32_t k, uint64_t seed, int32_t* s_out, double* y_out, double* y2_out,
+                    int32_t* s2_out) {
   if (n_rows < 0 || k < 1) return GMO_EINVAL;
   for (int32_t row = 0; row < n_rows; ++row) {
     int32_t* s = s_out + (int64_t)row * k;
     double* y = y_out + (int64_t)row * k;
     double* y2 = y2_out ? y2_out + (int64_t)row * k : NULL;
+    int32_t* s2 = s2_out ? s2_out + (int64_t)row * k : NULL;
     for (int32_t j = 0; j < k; ++j) {
       s[j] = INT32_MAX;
       y[j] = INFINITY;
       if (y2) y2[j] = INFINITY;
+      if (s2) s2[j] = INT32_MAX;
     }
     if (row_ptr[row + 1] < row_ptr[row]) return GMO_EINVAL;
     for (int64_t e = row_ptr[row]; e < row_ptr[row + 1]; ++e) {
@@ -304,17 +309,21 @@ int gmo_sketch_rows(const int64_t* row_ptr, const int32_t* ids, const double* w,
         if (!isfinite(b)) continue; /* reading R4 */
         if (better(b, id, y[c], s[c])) {
           if (y2) y2[c] = y[c];
+          if (s2) s2[c] = s[c];
           y[c] = b;
           s[c] = id;
-        } else if (y2 && b < y2[c]) {
+        } else if (y2 && better(b, id, y2[c], s2 ? s2[c] : INT32_MAX)) {
           y2[c] = b;
+          if (s2) s2[c] = id;
         }
       }
       stream_free(&st);
       if (rc) return rc;
     }
-    for (int32_t j = 0; j < k; ++j)
+    for (int32_t j = 0; j < k; ++j) {
       if (s[j] == INT32_MAX) s[j] = -1;
+      if (s2 && s2[j] == INT32_MAX) s2[j] = -1;
+    }
   }
   return GMO_OK;
 }

@@ -974,13 +974,18 @@ extern "C" int gm_row_ystar(const double* y, int32_t n_rows, int32_t k, double* 
 //
 // In host code `g_noalloc_scratch` is only a host-side stand-in for the symbol,
 // not a device address, so its device address is looked up with
-// cudaGetSymbolAddress once per device (with that device current) and cached.
+// cudaGetSymbolAddress with the device current: on every call made outside
+// stream capture (so that an address from before a cudaDeviceReset is never
+// reused), and taken from the per-device cache during capture.
 // ---------------------------------------------------------------------------
 #include <mutex>
 
 namespace gm {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = ws_bytes(GM_NOALLOC_MAX_ROWS, GM_NOALLOC_MAX_NNZ, GM_MAX_K);
+// 10,782,208 bytes (about 10.8 MB, 10.3 MiB): two 4 MiB element lists, 2 MiB of
+// long-row registers, the per-row index and the small tables.
+static_assert(NOALLOC_SCRATCH_BYTES == 10782208, "the documented size of the no-alloc scratch changed");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
@@ -988,12 +993,18 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 static std::mutex g_noalloc_mutex;
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
-static int noalloc_scratch(void** out) {
+// Device address of g_noalloc_scratch on the current device: looked up afresh
+// unless `stream` is capturing, then taken from the cache of an earlier call.
+static int noalloc_scratch(cudaStream_t stream, void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return GM_ECUDA;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+    cudaGetLastError();  // clear it; use the cache below
+    cap = cudaStreamCaptureStatusActive;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_noalloc_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GM_ECUDA;
     g_noalloc_ptr[dev] = p;
@@ -1007,17 +1018,23 @@ static int noalloc_scratch(void** out) {
 extern "C" int gm_sketch_noalloc(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
                                  int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out,
                                  double* y_out, void* stream) {
-  if (nnz > GM_NOALLOC_MAX_NNZ) return GM_ENOMEM;  // the fixed scratch is too small for this input
-  if (flags & GM_FLAG_VALIDATE) return GM_EINVAL;  // no way to read a device status back
+  if (nnz > GM_NOALLOC_MAX_NNZ || n_rows > GM_NOALLOC_MAX_ROWS) return GM_ENOMEM;  // beyond the fixed scratch
   const size_t need = gm_sketch_workspace_bytes(n_rows, nnz, k, flags);
   if (need == 0) return GM_EINVAL;
   if (need > gm::NOALLOC_SCRATCH_BYTES) return GM_ENOMEM;
   void* scratch = nullptr;
-  const int rc = gm::noalloc_scratch(&scratch);
+  const int rc = gm::noalloc_scratch((cudaStream_t)stream, &scratch);
   if (rc != GM_OK) return rc;
   // The first kernel of every call zeroes the scratch header (status, row counter,
   // counters) and rewrites the 1/(k-z) table; the heavy list is written before it
   // is read.  No other state carries over from the previous call.
   return gm::launch_sketch(row_ptr, ids, w, n_rows, nnz, k, seed, flags, s_out, y_out, scratch,
                            gm::NOALLOC_SCRATCH_BYTES, (cudaStream_t)stream, false, nullptr);
+}
+
+extern "C" int gm_sketch_noalloc_status(gm_stats* stats, void* stream) {
+  void* scratch = nullptr;
+  const int rc = gm::noalloc_scratch((cudaStream_t)stream, &scratch);
+  if (rc != GM_OK) return rc;
+  return gm_status(scratch, stats, stream);
 }

@@ -157,7 +157,8 @@ def pin_server_uniformity(k=8, n_elem=20000, seed=5):
 
 def pin_brute_force(seed=7):
     """P10: tiny vectors; the full arrival matrix (k arrivals of every element,
-    placed by server) and its column minima (Eq. sjv / yjpi) give the sketch."""
+    placed by server) and its column minima (Eq. sjv / yjpi) give the sketch, and
+    the second entry of each column in (time, id) order its runner-up."""
     fails = []
     rng = np.random.default_rng(seed)
     for trial in range(60):
@@ -174,9 +175,16 @@ def pin_brute_force(seed=7):
         want_y = M.min(axis=0)
         want_s = np.array([int(ids[np.flatnonzero(M[:, j] == want_y[j])].min()) if np.isfinite(want_y[j]) else -1
                            for j in range(k)])
-        s, y = oracle.sketch([0, n], ids, w, k, 99)
+        want_y2, want_s2 = np.full(k, np.inf), np.full(k, -1)
+        for j in range(k):
+            cand = sorted((M[a, j], int(ids[a])) for a in range(n) if np.isfinite(M[a, j]))
+            if len(cand) >= 2:
+                want_y2[j], want_s2[j] = cand[1]
+        s, y, y2, s2 = oracle.sketch([0, n], ids, w, k, 99, runner_up=True)
         if not (np.array_equal(s[0], want_s) and np.array_equal(y[0], want_y)):
             fails.append("brute force trial %d: %s %s vs %s %s" % (trial, s[0], y[0], want_s, want_y))
+        if not (np.array_equal(s2[0], want_s2) and np.array_equal(y2[0], want_y2)):
+            fails.append("brute force runner-up trial %d: %s %s vs %s %s" % (trial, s2[0], y2[0], want_s2, want_y2))
     return fails
 
 

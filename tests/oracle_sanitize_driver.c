@@ -13,7 +13,7 @@ double gmo_uniform_from_words(uint32_t w0, uint32_t w1);
 int gmo_exact_sum(const double* t, int64_t n, double* out);
 int gmo_arrivals(int32_t id, double v, int32_t k, uint64_t seed, int32_t n_steps, double* b_out, int32_t* c_out);
 int gmo_sketch_rows(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int32_t k,
-                    uint64_t seed, int32_t* s_out, double* y_out, double* y2_out);
+                    uint64_t seed, int32_t* s_out, double* y_out, double* y2_out, int32_t* s2_out);
 int gmo_fastsearch_budgets(const double* v, int64_t n, int64_t R, int64_t* out);
 int gmo_fastgm_alg1(const int32_t* ids, const double* w, int64_t n, int32_t k, uint64_t seed, int32_t delta,
                     int32_t* s, double* y, int64_t* arrivals_out, int64_t* search_R_out,
@@ -66,8 +66,8 @@ int main(void) {
     w[7] = 1.0;
     int32_t s[6 * 64], s2[6 * 64];
     double y[6 * 64], y2[6 * 64], ym[6 * 64], card[6], jac[6];
-    CHECK(gmo_sketch_rows(row_ptr, ids, w, n_rows, k, 11, s, y, y2));
-    CHECK(gmo_sketch_rows(row_ptr, ids, w, n_rows, k, 12, s2, ym, NULL));
+    CHECK(gmo_sketch_rows(row_ptr, ids, w, n_rows, k, 11, s, y, y2, s2));
+    CHECK(gmo_sketch_rows(row_ptr, ids, w, n_rows, k, 12, s2, ym, NULL, NULL));
     CHECK(gmo_jaccard(s, s2, n_rows, k, jac));
     if (k >= 2) CHECK(gmo_cardinality(y, n_rows, k, card));
     CHECK(gmo_merge(s, y, s2, ym, (int64_t)n_rows * k, s2, ym));

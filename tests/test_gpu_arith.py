@@ -16,7 +16,7 @@ import torch
 
 import oracle
 from paper_2302_05176_gb300 import build as libbuild
-from paper_2302_05176_gb300.parity import ulp_distance
+from parity import ulp_distance
 
 pytestmark = pytest.mark.gpu
 vp = ctypes.c_void_p

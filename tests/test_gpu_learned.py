@@ -18,7 +18,7 @@ import oracle
 from oracle import mlp
 from paper_2302_05176_gb300 import gm, learned
 from paper_2302_05176_gb300 import workloads as W
-from paper_2302_05176_gb300.parity import compare_sketch
+from parity import compare_sketch
 
 pytestmark = pytest.mark.gpu
 
@@ -169,9 +169,10 @@ def test_learned_sketch_exact_for_any_model(k):
         if margin == -30.0:
             assert st["rows_fallback"] == 6  # every row with a positive weight falls back (2 long)
     # and against the oracle on the short rows
-    s_ref, y_ref, y2_ref = oracle.sketch_rows_parallel(X.row_ptr, X.ids, X.w, k, 77, np.array([1, 2, 5, 6]),
-                                                       want_y2=True)
-    rep = compare_sketch(s0.cpu().numpy()[[1, 2, 5, 6]], y0.cpu().numpy()[[1, 2, 5, 6]], s_ref, y_ref, y2_ref)
+    s_ref, y_ref, y2_ref, s2_ref = oracle.sketch_rows_parallel(X.row_ptr, X.ids, X.w, k, 77,
+                                                               np.array([1, 2, 5, 6]), runner_up=True)
+    rep = compare_sketch(s0.cpu().numpy()[[1, 2, 5, 6]], y0.cpu().numpy()[[1, 2, 5, 6]], s_ref, y_ref, y2_ref,
+                         s2_ref)
     assert rep["ok"], rep
 
 

@@ -10,7 +10,7 @@ import torch
 import oracle
 from paper_2302_05176_gb300 import gm
 from paper_2302_05176_gb300 import workloads as W
-from paper_2302_05176_gb300.parity import compare_sketch
+from parity import compare_sketch
 
 pytestmark = pytest.mark.gpu
 SEED = 31
@@ -47,8 +47,9 @@ def test_stream_equals_distinct_set(k):
     assert torch.equal(st.s, s_ref[0]) and torch.equal(st.y.view(torch.int64), y_ref[0].view(torch.int64))
     # the oracle's Algorithm 2 over the same stream (host, FP64)
     s_o, y_o, _ = oracle.stream_fastgm(sid, sw, k, SEED)
-    _, _, y2 = oracle.sketch(np.array([0, ids.size]), ids, w, k, SEED, want_y2=True)
-    rep = compare_sketch(st.s.cpu().numpy()[None], st.y.cpu().numpy()[None], s_o[None], y_o[None], y2)
+    s_f, y_f, y2, s2 = oracle.sketch(np.array([0, ids.size]), ids, w, k, SEED, runner_up=True)
+    assert np.array_equal(s_f[0], s_o) and np.array_equal(y_f[0], y_o)  # Algorithm 2 = the unpruned stream
+    rep = compare_sketch(st.s.cpu().numpy()[None], st.y.cpu().numpy()[None], s_o[None], y_o[None], y2, s2)
     assert rep["ok"], rep
 
 

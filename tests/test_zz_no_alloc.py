@@ -4,10 +4,12 @@ Some callers cannot give the library a workspace (their device memory belongs
 to a framework allocator, or they must never stall on cudaMalloc, or their
 binding can only pass input and output buffers).  gm_sketch_noalloc keeps its
 scratch in a fixed device array inside libgm instead.  This test calls it through
-the C-ABI, twice in a row on different inputs, and checks each result against
-gm_sketch on the same input, within the tolerance the other GPU tests use.  It
-builds its own inputs so it passes alone in a fresh process as well as after the
-rest of the suite.
+the C-ABI several times in a row on different inputs -- including a row longer
+than 32,768 elements at k = 4096, which uses the array's long-row regions and the
+1024-thread kernels -- and checks each result against gm_sketch on the same
+input, within the tolerance the other GPU tests use, and the array's device
+status through gm_sketch_noalloc_status.  It builds its own inputs so it passes
+alone in a fresh process as well as after the rest of the suite.
 """
 import ctypes
 
@@ -18,11 +20,12 @@ import torch
 from paper_2302_05176_gb300 import build as libbuild
 from paper_2302_05176_gb300 import gm
 from paper_2302_05176_gb300 import workloads as W
-from paper_2302_05176_gb300.parity import compare_sketch
+from parity import compare_sketch
 
 pytestmark = pytest.mark.gpu
 
 GM_NOALLOC_MAX_NNZ = 1 << 20
+GM_NOALLOC_MAX_ROWS = 1 << 16
 
 
 @pytest.fixture(scope="module")
@@ -32,6 +35,15 @@ def noalloc():
     vp = ctypes.c_void_p
     f.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32,
                   vp, vp, vp]
+    f.restype = ctypes.c_int
+    return f
+
+
+@pytest.fixture(scope="module")
+def noalloc_status():
+    lib = ctypes.CDLL(libbuild.build())
+    f = lib.gm_sketch_noalloc_status
+    f.argtypes = [ctypes.POINTER(gm.gm_stats), ctypes.c_void_p]
     f.restype = ctypes.c_int
     return f
 
@@ -58,12 +70,22 @@ def _run_reference(X, k, seed):
     return s.cpu().numpy(), y.cpu().numpy()
 
 
-def test_noalloc_matches_gm_sketch_twice(noalloc):
+def test_noalloc_matches_gm_sketch_twice(noalloc, noalloc_status):
     torch.cuda.set_device(0)
+    rng = np.random.default_rng(23)
+    long_row = [(np.sort(rng.choice(1 << 24, size=n, replace=False)).astype(np.int32),
+                 W.pareto_weights(rng, n, 1.2, 1e-3)) for n in (100_000, 3, 1500)]
     cases = [(W.lognormal_batch(seed=21, n_rows=48, median=500.0, hi=6000), 1024, 7),
-             (W.uniform_rows(seed=22, n_rows=9, n_pos=[0, 1, 40, 300, 2500, 7, 64, 1000, 3]), 256, 8)]
-    for X, k, seed in cases:  # two calls in a row through the shared scratch
+             (W.uniform_rows(seed=22, n_rows=9, n_pos=[0, 1, 40, 300, 2500, 7, 64, 1000, 3]), 256, 8),
+             (W.from_rows(long_row), 4096, 9)]
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for X, k, seed in cases:  # calls in a row through the shared scratch
         s, y = _run_noalloc(noalloc, X, k, seed)
+        st = gm.gm_stats()
+        assert noalloc_status(ctypes.byref(st), stream) == gm.GM_OK
+        # the counters are this call's: every positive element visited at least once
+        # (a row redone with a wider bound visits its elements again)
+        assert st.status == gm.GM_OK and st.elements >= int(np.count_nonzero(X.w > 0)) > 0
         s_ref, y_ref = _run_reference(X, k, seed)
         rep = compare_sketch(s, y, s_ref, y_ref)
         assert rep["ok"], rep
@@ -74,6 +96,8 @@ def test_noalloc_rejects_inputs_beyond_its_scratch(noalloc):
     # rejected on the host before any launch, so the pointers are never touched
     fake = ctypes.c_void_p(0x1000)
     rc = noalloc(fake, fake, fake, 1, GM_NOALLOC_MAX_NNZ + 1, 64, 1, 0, fake, fake, None)
+    assert rc == gm.GM_ENOMEM
+    rc = noalloc(fake, fake, fake, 2 * GM_NOALLOC_MAX_ROWS, 100, 64, 1, 0, fake, fake, None)
     assert rc == gm.GM_ENOMEM
     rc = noalloc(fake, fake, fake, 1, 10, gm.GM_MAX_K + 1, 1, 0, fake, fake, None)
     assert rc == gm.GM_EINVAL
