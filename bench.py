@@ -40,9 +40,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", default="all", choices=["all", "fastgm", "prepass"],
+    ap.add_argument("--only", default="all", choices=["all", "fastgm", "prepass", "pareto"],
                     help="fastgm: time only the FastGM step (the case profiled with ncu); prepass: only the "
-                         "learned bound's pre-pass (gm_learned_bound) at the seeded initial parameters")
+                         "learned bound's pre-pass (gm_learned_bound) at the seeded initial parameters; "
+                         "pareto: only FastGM on the heavy-tail batch (16 x 10^6 Pareto(1.2), k = 4096)")
     ap.add_argument("--k", type=int, default=K_MAIN, help="k of the --only fastgm step")
     ap.add_argument("--flags", type=int, default=0, help="gm_sketch flags of the --only fastgm step")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-bound ablation")
@@ -274,6 +275,31 @@ def _time_ms(fn, reps=5):
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def _timed_on(n_rows, nnz, k, steps, warmup, stream, L, call):
+    """Mean ms per call and per main-kernel launch (library events) of `call`."""
+    import torch
+    from paper_2302_05176_gb300 import gm
+    s_out = torch.empty((n_rows, k), dtype=torch.int32, device="cuda")
+    y_out = torch.empty((n_rows, k), dtype=torch.float64, device="cuda")
+    ws = torch.empty(gm.sketch_workspace_bytes(n_rows, nnz, k), dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        call(s_out, y_out, ws)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for a, b in kev:
+        L.gm_diag_time_main_kernel(a.cuda_event, b.cuda_event)
+        call(s_out, y_out, ws)
+    L.gm_diag_time_main_kernel(None, None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    code, st = gm.gm_status(ws)
+    if code != gm.GM_OK:
+        raise RuntimeError("device status %s" % gm.strerror(code))
+    return (e0.elapsed_time(e1) / steps, float(np.mean([a.elapsed_time(b) for a, b in kev])), st, s_out, y_out)
 
 
 def max_sm_clock_mhz():
@@ -579,6 +605,18 @@ def main():
                               "gbs": (8 * nnz + 12 * n_rows + 8) / (ms * 1e-3) / 1e9}), flush=True)
         return
 
+    if args.only == "pareto":
+        P = W.pareto_heavy(seed=SEED, n_rows=16, n_pos=1_000_000)
+        prp, pids, pw = gm.to_device(P)
+        ms, kms, st, _, _ = _timed_on(P.n_rows, P.nnz, 4096, args.steps, args.warmup, stream, L,
+                                      lambda s_o, y_o, ws: gm.gm_sketch(prp, pids, pw, 4096, SEED, flags=args.flags,
+                                                                        s_out=s_o, y_out=y_o, ws=ws))
+        if rank == 0:
+            print(json.dumps({"only": "pareto k=4096 flags=%d" % args.flags, "ms": ms, "kernel_ms": kms,
+                              "hbm_gbs": algorithmic_bytes(P.nnz, P.n_rows, 4096) / (kms * 1e-3) / 1e9,
+                              "stats": st}), flush=True)
+        return
+
     # autotuned stream shapes and first-pass quantile per (k, row-length bucket), untimed;
     # --tuning-file reuses a saved table (so that a profiled run times the same tuning)
     tuned = {}
@@ -605,9 +643,14 @@ def main():
     ms_main, kms_main, st_main, s_main, y_main = timed(sketch_call(gm.gm_sketch, K_MAIN), K_MAIN, args.steps,
                                                        args.warmup)
     clk = clocks.stop()
-    ms_alt, kms_alt, st_alt, _, _ = timed(sketch_call(gm.gm_sketch, K_ALT), K_ALT, max(2, args.steps // 3),
-                                          args.warmup)
-    ms_plain, _, st_plain, _, _ = timed(sketch_call(gm.gm_sketch_plain, K_MAIN), K_MAIN, args.plain_steps, 1)
+    ms_alt, kms_alt, st_alt, s_alt, y_alt = timed(sketch_call(gm.gm_sketch, K_ALT), K_ALT, max(2, args.steps // 3),
+                                                  args.warmup)
+    ms_plain, _, st_plain, s_pl, y_pl = timed(sketch_call(gm.gm_sketch_plain, K_MAIN), K_MAIN, args.plain_steps, 1)
+    same_plain = bool(torch.equal(s_pl, s_main) and torch.equal(y_pl.view(torch.int64), y_main.view(torch.int64)))
+    del s_pl, y_pl
+    ms_plain4, _, st_plain4, s_pl, y_pl = timed(sketch_call(gm.gm_sketch_plain, K_ALT), K_ALT, 1, 1)
+    same_plain4 = bool(torch.equal(s_pl, s_alt) and torch.equal(y_pl.view(torch.int64), y_alt.view(torch.int64)))
+    del s_pl, y_pl, s_alt, y_alt
 
     # end to end through the C-ABI with host buffers (gm_sketch_host): H2D of the inputs
     # and D2H of the registers inside the timed region, every step
@@ -647,8 +690,15 @@ def main():
                   "elements_per_s": world * nnz / (ms_alt * 1e-3),
                   "roofline_frac": alu_roofline(st_alt, kms_alt)["frac"]},
         "plain_k1024": {"sketches_per_s": world * n_rows / (ms_plain * 1e-3), "ms_per_step": ms_plain,
-                        "arrivals_per_s": st_plain["arrivals"] / (ms_plain * 1e-3)},
+                        "elements_per_s": world * nnz / (ms_plain * 1e-3),
+                        "arrivals_per_s": st_plain["arrivals"] / (ms_plain * 1e-3),
+                        "identical_to_fastgm": same_plain},
         "speedup_vs_plain_k1024": ms_plain / ms_main,
+        "plain_k4096": {"sketches_per_s": world * n_rows / (ms_plain4 * 1e-3), "ms_per_step": ms_plain4,
+                        "elements_per_s": world * nnz / (ms_plain4 * 1e-3),
+                        "arrivals_per_s": st_plain4["arrivals"] / (ms_plain4 * 1e-3),
+                        "identical_to_fastgm": same_plain4},
+        "speedup_vs_plain_k4096": ms_plain4 / ms_alt,
         "roofline": alu_roofline(st_main, kms_main),
         "hbm": hbm_figures(nnz, n_rows, K_MAIN, kms_main),
         "fp64_view": fp64_pipe_view(st_main["kept"], kms_main),
