@@ -287,6 +287,9 @@ def _timed_on(n_rows, nnz, k, steps, warmup, stream, L, call):
     for _ in range(warmup):
         call(s_out, y_out, ws)
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in kev:  # materialise the event handles the library records
+        a.record(stream)
+        b.record(stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)

@@ -78,10 +78,20 @@ extern "C" {
  * escalation paths.  The registers are the same; only the work grows. */
 #define GM_FLAG_TIGHT_BOUND (1u << 3)
 /* Initial pruning bound per row (Sec. 2.2 FastSearch / FastPrune).  Any bound
- * gives the same registers; it only changes how many arrivals are generated. */
-#define GM_BOUND_CLOSED (0u << 4)  /* closed-form quantile of y* (default)          */
-#define GM_BOUND_NONE (1u << 4)    /* no initial bound: prune only by the running y* */
-#define GM_BOUND_LEARNED (2u << 4) /* per-row bound from a trained model (gm_model_*) */
+ * gives the same registers; it only changes how many arrivals are generated.
+ *   GM_BOUND_CLOSED: the (1 - p) quantile of y* given sum v (the law of y* sum v
+ *     is that of the largest of k Exp(1), Sec. 2.3), then wider passes.
+ *   GM_BOUND_NONE: FastGM without prior knowledge of y*: FastSearch's release
+ *     horizon starts at R = k arrivals per row (T = 1 / sum v) and doubles until
+ *     every register is filled (each pass regenerates the arrivals below its T;
+ *     register updates are idempotent minima).  A row cut into chunks runs the
+ *     same ladder per chunk on the chunk's own registers, and once the row's
+ *     merged registers are all filled a chunk stops every stream at their largest
+ *     value y* (FastPrune).
+ *   GM_BOUND_LEARNED: per-row bound from a trained model (gm_model_*). */
+#define GM_BOUND_CLOSED (0u << 4)
+#define GM_BOUND_NONE (1u << 4)
+#define GM_BOUND_LEARNED (2u << 4)
 #define GM_BOUND_MASK (3u << 4)
 
 /* ---- device-side counters, read back by gm_status ------------------------- */

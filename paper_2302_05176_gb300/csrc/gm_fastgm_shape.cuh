@@ -308,9 +308,9 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
     bool last = !(Tf < 3.0e38f) || pass >= 12;
     if (!last) {
       Td = f64_from_f32(Tf);
-      for (int p = 1; p < pass; ++p) {  // passes >= 2 widen the bound by 16x each
-        Td *= 16.0;
-        Tf *= 16.0f;  // exact: the screen needs Tf = Td as reals, so no clamp below Td
+      for (int p = 1; p < pass; ++p) {  // passes >= 2 widen the bound by a.grow each
+        Td *= (double)a.grow;
+        Tf *= a.grow;  // exact (a power of two): the screen needs Tf = Td as reals, so no clamp below Td
       }
       if (!(Td < 1.0e300) || !(Tf < 3.0e38f)) last = true;
     }
@@ -365,6 +365,46 @@ __device__ __forceinline__ void finish_long(const SketchArgs& a, int row, int lo
   }
 }
 
+// Bound of pass `pass` of a bound-free long-row chunk: FastSearch's doubling
+// horizon 2^pass / (the chunk's sum), unless the row's merged registers g are all
+// filled, when their largest value y* (rounded up to FP32) is used instead if
+// smaller: every final register of the row is at most y*, so no arrival above it
+// can matter (FastPrune), and that pass is the chunk's last (returns true).
+// Block-wide (barriers); every thread gets the same result.
+__device__ __forceinline__ bool ladder_bound(const Reg* g, int k, float sumc, int pass, SmemScalars& sh,
+                                             uint64_t& Tbits, float& Tf) {
+  unsigned long long m = 0ull;
+  for (int j = threadIdx.x; j < k; j += BLOCK) {
+    const unsigned long long y = __ldcg(&g[j].y);
+    m = y > m ? y : m;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(FULL, m, d);
+    m = o > m ? o : m;
+  }
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(sh.red_d);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0ull;
+  for (int q = 0; q < WARPS; ++q) m = red[q] > m ? red[q] : m;
+  __syncthreads();
+  float T = __int_as_float(0x7F800000);
+  if (pass < 40) T = ldexpf(1.0f, pass) / sumc;  // beyond: no bound at all
+  bool final = !(T < 3.0e38f);
+  if (m < INF_BITS) {  // every register of the row is filled: FastPrune by its y*
+    const float ty = fmaxf(__double2float_ru(__longlong_as_double((long long)m)), 1.17549435e-38f);
+    if (ty <= T) {
+      T = ty;
+      final = true;
+    }
+  }
+  const bool none = !(T < 3.0e38f);
+  Tbits = none ? DBL_MAX_BITS : (uint64_t)__double_as_longlong(f64_from_f32(T));
+  Tf = none ? __int_as_float(0x7F800000) : T;
+  return final;
+}
+
 template <int ARITH, int MODE>
 __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -406,24 +446,43 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
       __syncthreads();
       continue;
     }
-    // one chunk of a long row, bound from the row's sum (rowsum kernel)
+    // one chunk of a long row, bound from the row's sum (rowsum kernel); in the
+    // bound-free mode a ladder of passes on the chunk's own registers instead
     const int64_t clo = lo + (int64_t)chunk * SPLIT_LEN;
     const int64_t chi = min(hi, clo + SPLIT_LEN);
     const LongRow lr = a.longs[longi];
+    Reg* g = a.long_regs + (int64_t)longi * k;
     if (lr.npos > 0 && chi > clo) {
-      uint64_t Tbits;
-      float Tf;
-      chunk_bound(a, row, lr.sum, Tbits, Tf);
-      reset_lists(sh);
-      __syncthreads();
+      float tdummy;
+      const bool ladder = a.chunk_ladder && !row_bound(a, row, tdummy);
+      float sumc = 0.0f;
+      int nposc = 1;
       long long t = read_clock();
-      light_phase<ARITH>(a, clo, (int)(chi - clo), Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt,
-                         gave_up);
-      clk_add(cnt, CLK_LIGHT, t);
-      __syncthreads();
-      clk_add(cnt, CLK_WAIT, t);
-      warp_phases<ARITH>(a, clo, (int)(chi - clo), Tbits, regs, area, dense, sh, cnt, gave_up, t);
-      Reg* g = a.long_regs + (int64_t)longi * k;
+      if (ladder) block_sum<BLOCK>(a, clo, (int)(chi - clo), sh.red_f, sh.red_i, sumc, nposc);
+      for (int pass = 0; nposc > 0; ++pass) {
+        uint64_t Tbits;
+        float Tf;
+        bool final = true;
+        if (ladder)
+          final = ladder_bound(g, k, sumc, pass, sh, Tbits, Tf);
+        else
+          chunk_bound(a, row, lr.sum, Tbits, Tf);
+        reset_lists(sh);
+        __syncthreads();
+        clk_add(cnt, CLK_SETUP, t);
+        light_phase<ARITH>(a, clo, (int)(chi - clo), Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh,
+                           cnt, gave_up);
+        clk_add(cnt, CLK_LIGHT, t);
+        __syncthreads();
+        clk_add(cnt, CLK_WAIT, t);
+        warp_phases<ARITH>(a, clo, (int)(chi - clo), Tbits, regs, area, dense, sh, cnt, gave_up, t);
+        if (final) break;
+        // the chunk's own sketch is exact once its registers are all at or below T
+        int empty = 0;
+        for (int j = tid; j < k; j += BLOCK) empty |= (regs[j].y > Tbits);
+        if (!__syncthreads_or(empty)) break;
+        if (tid == 0) ++cnt.escalated;
+      }
       for (int j = tid; j < k; j += BLOCK) {
         const Reg r = regs[j];
         if (r.y != INF_BITS) global_lower(&g[j], r.y, r.id, gave_up);

@@ -102,7 +102,9 @@ struct SketchArgs {
   uint32_t* esc;
   int max_long;
   int ndense;             // dense permutations per CTA (warps that take super-heavy elements)
-  float q1, q2, q_split;  // normalised bounds: first pass, later passes, long rows (inf = none)
+  float q1, q2, q_split;  // normalised bounds: first pass, second pass, long rows (inf = none)
+  float grow;             // factor of each later pass's bound over the one before (a power of two)
+  int chunk_ladder;       // bound-free: long-row chunks grow their own bound, pruned by the row's y*
   const float* t_row;     // learned first-pass bound per row (absolute), or null
   float light_max, medium_max, heavy_max;  // routing thresholds (expected arrivals below T)
   const int32_t* init_s;  // stream mode (one row): registers start from this sketch, else unfilled
@@ -615,11 +617,21 @@ static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const
   a.medium_max = tn.medium_max;
   a.heavy_max = tn.heavy_max;
   if (bound == GM_BOUND_NONE) {
-    a.q1 = a.q2 = a.q_split = INFINITY;
+    // FastSearch without prior knowledge of y*: the release horizon starts at R = k
+    // arrivals per row (T = 1 / sum v) and doubles until every register is filled;
+    // long-row chunks run the same ladder on their own registers, pruned by the
+    // row's merged y* once it is finite (FastPrune), so no long row is redone.
+    a.q1 = 1.0f;
+    a.q2 = 2.0f;
+    a.grow = 2.0f;
+    a.q_split = INFINITY;
+    a.chunk_ladder = 1;
   } else {
     a.q1 = (float)quantile_bound((double)tn.p_first, k);
     a.q2 = (float)quantile_bound(1e-6, k);
     a.q_split = (float)quantile_bound(1e-3, k);
+    a.grow = 16.0f;
+    a.chunk_ladder = 0;
     if (flags & GM_FLAG_TIGHT_BOUND) {
       a.q1 *= 0.125f;
       a.q_split *= 0.125f;

@@ -285,8 +285,10 @@ def test_trained_bound_fallback_rate_and_gain():
         f = gm.gm_features(rp, ids, w, k)
         pred = model.predict(f) + f[:, 1]
         assert abs(float(pred.mean()) - mlp.ystar_quantile(tau, k)) < 0.05, k
-    # held-out batch: the learned bound falls back in about 1 - tau of the rows,
-    # and does far less work than no initial bound
+    # held-out batch: the learned bound falls back in about 1 - tau of the rows; it
+    # keeps fewer arrivals than FastGM without an initial bound (FastSearch's doubling
+    # horizon, the method without the network) and about as many as the closed-form
+    # quantile, which is the information limit (y* sum v has the same law for every row)
     rp, ids, w = W.lognormal_batch_device(4242, n_rows=4096)
     k = 1024
     s_l, y_l, ws_l = model.sketch(rp, ids, w, k, 3)
@@ -299,5 +301,6 @@ def test_trained_bound_fallback_rate_and_gain():
     assert torch.equal(s_n, s_c) and torch.equal(y_n.view(torch.int64), y_c.view(torch.int64))
     rate = st_l["rows_fallback"] / 4096
     assert abs(rate - (1 - tau)) < 4 * math.sqrt(tau * (1 - tau) / 4096) + 0.02, rate
-    assert st_l["kept"] < 0.5 * st_n["kept"]
+    assert st_l["kept"] < 0.8 * st_n["kept"]
+    assert abs(st_l["kept"] / st_c["kept"] - 1.0) < 0.1
     assert 0.8 < st_l["kept"] / st_c["kept"] < 1.25

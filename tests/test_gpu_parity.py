@@ -137,12 +137,41 @@ def test_wide_shape_long_rows_and_escalations(tight):
 
 
 def test_bound_modes_agree():
+    """FastGM without an initial bound (FastSearch's doubling horizon from 1/sum v,
+    long-row chunks pruned by the row's merged y*) gives the closed form's
+    registers; it keeps more arrivals, but of the same order (not the k n+ of the
+    unpruned stream)."""
     X = W.lognormal_batch(seed=9, n_rows=16, median=400.0, hi=2000)
     k = 512
     s0, y0, st0 = run(gm.gm_sketch, X, k, 3, flags=gm.GM_BOUND_CLOSED)
     s1, y1, st1 = run(gm.gm_sketch, X, k, 3, flags=gm.GM_BOUND_NONE)
     assert np.array_equal(s0, s1) and np.array_equal(y0.view(np.int64), y1.view(np.int64))
-    assert st0["arrivals"] < st1["arrivals"]
+    assert st0["kept"] < st1["kept"] < 4 * st0["kept"]
+    assert st1["kept"] < 0.2 * k * X.nnz
+
+
+@pytest.mark.parametrize("k", [128, 4096])
+def test_bound_free_long_rows_against_oracle(k):
+    """The bound-free mode on rows cut into chunks (each chunk grows its own bound
+    until its registers fill or the row's merged y* is finite) and on short rows,
+    against the oracle; at k = 4096 against the plain sketch too."""
+    rng = np.random.default_rng(41)
+    rows = []
+    for n in (70_000, 33_000, 5, 40_000, 1200, 0, 1):
+        ids = np.sort(rng.choice(1 << 24, size=n, replace=False)).astype(np.int32)
+        rows.append((ids, W.pareto_weights(rng, n, 1.2, 1e-3) if n % 2 else rng.standard_exponential(n)))
+    X = W.from_rows(rows)
+    if k == 128:
+        check(X, k, 5, flags=gm.GM_FLAG_VALIDATE | gm.GM_BOUND_NONE, variants=("fastgm", "fastgm_int"))
+    else:
+        s0, y0, st0 = run(gm.gm_sketch, X, k, 5, flags=gm.GM_FLAG_VALIDATE | gm.GM_BOUND_NONE)
+        s1, y1, _ = run(gm.gm_sketch_plain, X, k, 5)
+        assert np.array_equal(s0, s1) and np.array_equal(y0.view(np.int64), y1.view(np.int64))
+        sub = np.array([2, 4, 6])  # the short rows against the oracle
+        s_ref, y_ref, y2_ref, s2_ref = oracle.sketch_rows_parallel(X.row_ptr, X.ids, X.w, k, 5, sub,
+                                                                   runner_up=True)
+        rep = compare_sketch(s0[sub], y0[sub], s_ref, y_ref, y2_ref, s2_ref)
+        assert rep["ok"], rep
 
 
 def test_seed_changes_sketch_and_repeat_is_deterministic():
@@ -322,6 +351,9 @@ def test_pareto_heavy_full_size():
     s, y, _ = gm.gm_sketch(rp, ids, w, k, seed)
     sp, yp, _ = gm.gm_sketch_plain(rp, ids, w, k, seed)
     assert torch.equal(s, sp) and torch.equal(y.view(torch.int64), yp.view(torch.int64))
+    sn, yn, wsn = gm.gm_sketch(rp, ids, w, k, seed, flags=gm.GM_BOUND_NONE)
+    assert torch.equal(s, sn) and torch.equal(y.view(torch.int64), yn.view(torch.int64))
+    assert gm.gm_status(wsn)[1]["arrivals"] < 0.05 * X.nnz * k  # pruned, though without an initial bound
     lo, hi = X.row_ptr[0], X.row_ptr[1]
     s_ref, y_ref, _ = oracle.fastgm_alg1(X.ids[lo:hi], X.w[lo:hi], k, seed)
     rep = compare_sketch(s[0].cpu().numpy(), y[0].cpu().numpy(), s_ref, y_ref)
