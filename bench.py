@@ -220,10 +220,13 @@ def fp64_pipe_view(kept, kernel_ms):
 
 
 def estimator_figures(s, y):
-    """The estimators and the union on the benchmark batch's sketches, each against
-    HBM with L2 flushed before every call: Jaccard of rows (i, i+1) reads 2 x 4k
-    bytes per pair, cardinality 8k per row, the union 2 x 12k in and 12k out per
-    row (8 bytes out per estimate)."""
+    """The estimators and the union on the benchmark batch's sketches, against HBM:
+    Jaccard of rows (i, i+1) reads 2 x 4k bytes per pair, cardinality 8k per row,
+    the union 2 x 12k in and 12k out per row (8 bytes out per estimate).  Each is
+    timed two ways: on the batch's sketches with L2 flushed before every call and
+    the device time taken by events the library records right around its kernel
+    (`ms`, `gbs`, `hbm_frac`); and on the sketches repeated 8 times (268 MB of ids
+    for Jaccard, more than the 129 MB L2), 10 calls back to back (`large`)."""
     import torch
     from paper_2302_05176_gb300 import gm
     n, k = s.shape
@@ -236,10 +239,50 @@ def estimator_figures(s, y):
     for name, fn, nbytes in (("jaccard", lambda: gm.gm_jaccard(s, s_b, out=jo), n * (8 * k + 8)),
                              ("cardinality", lambda: gm.gm_cardinality(y, out=co), n * (8 * k + 8)),
                              ("merge", lambda: gm.gm_merge(s, y, s_b, y_b, s_out=ms_, y_out=my_), n * 36 * k)):
-        ms = _time_ms_cold(fn)
+        ms = _time_aux_cold(fn)
         gbs = nbytes / (ms * 1e-3) / 1e9
-        out[name] = {"ms": ms, "algorithmic_bytes": nbytes, "gbs": gbs, "hbm_frac": gbs / hbm_gbs}
+        out[name] = {"ms": ms, "algorithmic_bytes": nbytes, "gbs": gbs, "hbm_frac": gbs / hbm_gbs,
+                     "host_timed_ms": _time_ms_cold(fn)}
+    rep = 8
+    S, Y = s.repeat(rep, 1), y.repeat(rep, 1)
+    S_b, Y_b = torch.roll(S, 1, 0).contiguous(), torch.roll(Y, 1, 0).contiguous()
+    JO = torch.empty(n * rep, dtype=torch.float64, device=s.device)
+    CO = torch.empty(n * rep, dtype=torch.float64, device=s.device)
+    MS, MY = torch.empty_like(S), torch.empty_like(Y)
+    for name, fn, nbytes in (("jaccard", lambda: gm.gm_jaccard(S, S_b, out=JO), rep * n * (8 * k + 8)),
+                             ("cardinality", lambda: gm.gm_cardinality(Y, out=CO), rep * n * (8 * k + 8)),
+                             ("merge", lambda: gm.gm_merge(S, Y, S_b, Y_b, s_out=MS, y_out=MY), rep * n * 36 * k)):
+        ms = _time_ms(fn, reps=10)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name]["large"] = {"rows": rep * n, "ms": ms, "algorithmic_bytes": nbytes, "gbs": gbs,
+                              "hbm_frac": gbs / hbm_gbs}
     return out
+
+
+def _time_aux_cold(fn, reps=10):
+    """Mean device time of the library kernels of fn(), from events the library
+    records immediately before its first and after its last kernel
+    (gm_diag_time_aux_kernels), with L2 flushed (a 256 MB write) before each call."""
+    import ctypes
+    import torch
+    from paper_2302_05176_gb300 import gm
+    L = gm.lib()
+    L.gm_diag_time_aux_kernels.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    if not _FLUSH:
+        _FLUSH.append(torch.empty(256 << 20, dtype=torch.uint8, device="cuda"))
+    fn()
+    total = 0.0
+    for _ in range(reps):
+        _FLUSH[0].zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        e1.record()
+        L.gm_diag_time_aux_kernels(e0.cuda_event, e1.cuda_event)
+        fn()
+        L.gm_diag_time_aux_kernels(None, None)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / reps
 
 
 _FLUSH = []
@@ -602,7 +645,7 @@ def main():
         call = lambda: gm.gm_learned_bound(rp, w, args.k, params, 0.0, out=t_out, ws=lb_ws)
         for _ in range(max(3, args.warmup)):
             call()
-        ms = _time_ms_cold(call, reps=args.steps)
+        ms = _time_aux_cold(call, reps=args.steps)
         if rank == 0:
             print(json.dumps({"only": "prepass k=%d" % args.k, "ms": ms,
                               "gbs": (8 * nnz + 12 * n_rows + 8) / (ms * 1e-3) / 1e9}), flush=True)
@@ -1002,7 +1045,7 @@ def learned_ablation(args, timed, sketch_call, dev_csr, s_main, y_main, ms_main,
     t_out = torch.empty(n_rows, dtype=torch.float32, device=rp.device)
     lb_ws = torch.empty(gm.lib().gm_learned_bound_workspace_bytes(n_rows, w.numel()), dtype=torch.uint8,
                         device=rp.device)
-    pre_ms = _time_ms_cold(lambda: gm.gm_learned_bound(rp, w, K_MAIN, params, 0.0, out=t_out, ws=lb_ws))
+    pre_ms = _time_aux_cold(lambda: gm.gm_learned_bound(rp, w, K_MAIN, params, 0.0, out=t_out, ws=lb_ws))
     pre_bytes = 8 * w.numel() + 8 * (n_rows + 1) + 4 * n_rows
     hbm_gbs, hbm_src = peaks()
     return {

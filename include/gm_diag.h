@@ -71,6 +71,13 @@ int gm_diag_fma(int32_t fp64, int32_t blocks, int32_t iters, void* out, void* st
  * for timing only.  GM_EINVAL if exactly one of the two is NULL. */
 int gm_diag_time_main_kernel(void* before, void* after);
 
+/* The same for the kernels of gm_jaccard, gm_cardinality, gm_merge and
+ * gm_learned_bound: every later call of one of them records `before` on its
+ * stream immediately before its first kernel and `after` immediately after its
+ * last, so that its device time excludes the host's launch overhead.
+ * Process-wide, not thread-safe: for timing only. */
+int gm_diag_time_aux_kernels(void* before, void* after);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,14 +37,27 @@ __device__ __forceinline__ double warp_jaccard(const int32_t* __restrict__ a, co
   return (double)hits / (double)k;
 }
 
-// (k - 1) / sum_j y_j by one warp: lane l adds y[l], y[l + 32], ... in order
-// (eight loads in flight), then a butterfly over the lanes; every lane returns
-// it.  An unfilled register (+inf) gives 0.
+// (k - 1) / sum_j y_j by one warp; every lane returns it.  When the row is 16-byte
+// aligned and k is even, lane l adds the pairs (y[2l], y[2l+1]), (y[2l+64],
+// y[2l+65]), ... in order (16-byte loads, four in flight), else y[l], y[l + 32],
+// ... (eight in flight); then a butterfly over the lanes.  An unfilled register
+// (+inf) gives 0.
 __device__ __forceinline__ double warp_cardinality(const double* __restrict__ y, int k) {
   const int lane = threadIdx.x & 31;
   double s = 0.0;
+  if ((k & 1) == 0 && (reinterpret_cast<uintptr_t>(y) & 15u) == 0) {
+    const double2* y2 = reinterpret_cast<const double2*>(y);
+    const int k2 = k >> 1;
+#pragma unroll 4
+    for (int j = lane; j < k2; j += 32) {
+      const double2 v = __ldg(y2 + j);
+      s += v.x;
+      s += v.y;
+    }
+  } else {
 #pragma unroll 8
-  for (int j = lane; j < k; j += 32) s += __ldg(y + j);
+    for (int j = lane; j < k; j += 32) s += __ldg(y + j);
+  }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, d);
   return (double)(k - 1) / s;

@@ -3,9 +3,27 @@
 #include <cuda_runtime.h>
 
 #include "gm.h"
+#include "gm_diag.h"
 #include "gm_estim.cuh"
+#include "gm_internal.h"
 
 namespace gm {
+
+static cudaEvent_t g_aux_before = nullptr, g_aux_after = nullptr;
+
+void aux_events(cudaEvent_t* before, cudaEvent_t* after) {
+  *before = g_aux_before;
+  *after = g_aux_after;
+}
+
+// Launch `launch()` between the registered timing events, if any.
+template <class F>
+static int timed_launch(cudaStream_t st, F launch) {
+  if (g_aux_before) cudaEventRecord(g_aux_before, st);
+  launch();
+  if (g_aux_after) cudaEventRecord(g_aux_after, st);
+  return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
+}
 
 // One warp per pair: count equal, filled registers.
 __global__ void jaccard_kernel(const int32_t* __restrict__ sa, const int32_t* __restrict__ sb, int64_t n_pairs,
@@ -56,18 +74,21 @@ extern "C" int gm_jaccard(const int32_t* s_a, const int32_t* s_b, int64_t n_pair
   if (k < 1 || n_pairs < 0) return GM_EINVAL;
   if (n_pairs == 0) return GM_OK;
   if (!s_a || !s_b || !out) return GM_EINVAL;
-  gm::jaccard_kernel<<<gm::grid_for(n_pairs, gm::EST_BLOCK / 32), gm::EST_BLOCK, 0, (cudaStream_t)stream>>>(
-      s_a, s_b, n_pairs, k, out);
-  return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
+  const cudaStream_t st = (cudaStream_t)stream;
+  return gm::timed_launch(st, [&] {
+    gm::jaccard_kernel<<<gm::grid_for(n_pairs, gm::EST_BLOCK / 32), gm::EST_BLOCK, 0, st>>>(s_a, s_b, n_pairs, k,
+                                                                                             out);
+  });
 }
 
 extern "C" int gm_cardinality(const double* y, int32_t n_rows, int32_t k, double* out, void* stream) {
   if (k < 2 || n_rows < 0) return GM_EINVAL;
   if (n_rows == 0) return GM_OK;
   if (!y || !out) return GM_EINVAL;
-  gm::cardinality_kernel<<<gm::grid_for(n_rows, gm::EST_BLOCK / 32), gm::EST_BLOCK, 0, (cudaStream_t)stream>>>(
-      y, n_rows, k, out);
-  return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
+  const cudaStream_t st = (cudaStream_t)stream;
+  return gm::timed_launch(st, [&] {
+    gm::cardinality_kernel<<<gm::grid_for(n_rows, gm::EST_BLOCK / 32), gm::EST_BLOCK, 0, st>>>(y, n_rows, k, out);
+  });
 }
 
 extern "C" int gm_merge(const int32_t* s_a, const double* y_a, const int32_t* s_b, const double* y_b, int64_t n_regs,
@@ -75,7 +96,16 @@ extern "C" int gm_merge(const int32_t* s_a, const double* y_a, const int32_t* s_
   if (n_regs < 0) return GM_EINVAL;
   if (n_regs == 0) return GM_OK;
   if (!s_a || !y_a || !s_b || !y_b || !s_out || !y_out) return GM_EINVAL;
-  gm::merge_kernel<<<gm::grid_for(n_regs, gm::EST_BLOCK), gm::EST_BLOCK, 0, (cudaStream_t)stream>>>(
-      s_a, y_a, s_b, y_b, n_regs, s_out, y_out);
-  return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
+  const cudaStream_t st = (cudaStream_t)stream;
+  return gm::timed_launch(st, [&] {
+    gm::merge_kernel<<<gm::grid_for(n_regs, gm::EST_BLOCK), gm::EST_BLOCK, 0, st>>>(s_a, y_a, s_b, y_b, n_regs,
+                                                                                    s_out, y_out);
+  });
+}
+
+extern "C" int gm_diag_time_aux_kernels(void* before, void* after) {
+  if ((before == nullptr) != (after == nullptr)) return GM_EINVAL;
+  gm::g_aux_before = (cudaEvent_t)before;
+  gm::g_aux_after = (cudaEvent_t)after;
+  return GM_OK;
 }

@@ -59,24 +59,50 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
   Fix acc = fix_zero();
   int wcount = 0;
   bool pool_done = false;
+  // the warp's next screening batch, claimed and loaded one batch ahead so that its
+  // weight and id loads are in flight while the current batch is screened
+  int nbase = 0;
+  double nv = 0.0;
+  int32_t nid = 0;
+#if GM_SCREEN_PREFETCH
+  if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
+  nbase = __shfl_sync(FULL, nbase, 0);
+  if (nbase + lane < n) {
+    nv = __ldcs(a.w + lo + nbase + lane);
+    nid = __ldcs(a.ids + lo + nbase + lane);
+  }
+#endif
   while (true) {
     // hand survivors to idle lanes, screening new elements while some are idle
     uint32_t nmask = __ballot_sync(FULL, e < 0);
     while (nmask && !(pool_done && wcount == 0)) {
       if (wcount == 0) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&sh.pool, 32);
-        base = __shfl_sync(FULL, base, 0);
+#if !GM_SCREEN_PREFETCH
+        if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
+        nbase = __shfl_sync(FULL, nbase, 0);
+        if (nbase + lane < n) {
+          nv = a.w[lo + nbase + lane];
+          nid = a.ids[lo + nbase + lane];
+        }
+#endif
+        const int base = nbase;
         if (base >= n) {
           pool_done = true;
           break;
         }
         const int slot = base + lane;
         bool surv = false;
-        double v = 0.0;
-        int32_t idv = 0;
+        double v = nv;
+        int32_t idv = nid;
+#if GM_SCREEN_PREFETCH
+        if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
+        nbase = __shfl_sync(FULL, nbase, 0);
+        if (nbase + lane < n) {
+          nv = __ldcs(a.w + lo + nbase + lane);
+          nid = __ldcs(a.ids + lo + nbase + lane);
+        }
+#endif
         if (slot < n) {
-          v = a.w[lo + slot];
           if (positive_finite(v)) {
             ++cnt.elements;
             const float vf = f32_trunc(v);
@@ -90,7 +116,6 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
               else
                 a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | TAG_MEDIUM;
             } else {
-              idv = a.ids[lo + slot];
               const Words wd = philox((uint32_t)idv, 0u, a.key0, a.key1);
               if (screen_out(wd.w1, vf, Tf, kf))
                 ++cnt.screened;  // first arrival certainly above T: nothing of it counts
@@ -448,8 +473,8 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
     }
     // one chunk of a long row, bound from the row's sum (rowsum kernel); in the
     // bound-free mode a ladder of passes on the chunk's own registers instead
-    const int64_t clo = lo + (int64_t)chunk * SPLIT_LEN;
-    const int64_t chi = min(hi, clo + SPLIT_LEN);
+    const int64_t clo = lo + (int64_t)chunk * a.chunk_len;
+    const int64_t chi = min(hi, clo + a.chunk_len);
     const LongRow lr = a.longs[longi];
     Reg* g = a.long_regs + (int64_t)longi * k;
     if (lr.npos > 0 && chi > clo) {
@@ -483,10 +508,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
         if (!__syncthreads_or(empty)) break;
         if (tid == 0) ++cnt.escalated;
       }
-      for (int j = tid; j < k; j += BLOCK) {
-        const Reg r = regs[j];
-        if (r.y != INF_BITS) global_lower(&g[j], r.y, r.id, gave_up);
-      }
+      merge_to_global<BLOCK>(regs, g, k, gave_up);
     }
     __threadfence();
     __syncthreads();
@@ -528,8 +550,8 @@ __global__ void __launch_bounds__(BLOCK, 1) plain_kernel(SketchArgs a) {
     int64_t lo, hi;
     row_bounds(a, row, lo, hi);
     init_regs(a, regs, k);
-    const int64_t clo = longi < 0 ? lo : lo + (int64_t)chunk * SPLIT_LEN;
-    const int64_t chi = longi < 0 ? hi : min(hi, clo + SPLIT_LEN);
+    const int64_t clo = longi < 0 ? lo : lo + (int64_t)chunk * a.chunk_len;
+    const int64_t chi = longi < 0 ? hi : min(hi, clo + a.chunk_len);
     const int n = (int)(chi - clo);
     if (longi < 0) {
       float sumv;
@@ -580,11 +602,7 @@ __global__ void __launch_bounds__(BLOCK, 1) plain_kernel(SketchArgs a) {
       __syncthreads();
       continue;
     }
-    Reg* g = a.long_regs + (int64_t)longi * k;
-    for (int j = tid; j < k; j += BLOCK) {
-      const Reg r = regs[j];
-      if (r.y != INF_BITS) global_lower(&g[j], r.y, r.id, gave_up);
-    }
+    merge_to_global<BLOCK>(regs, a.long_regs + (int64_t)longi * k, k, gave_up);
     __threadfence();
     __syncthreads();
     if (tid == 0) sh.last = (atomicAdd(&a.longs[longi].done, 1u) == a.longs[longi].nchunks - 1) ? 1 : 0;
@@ -624,13 +642,31 @@ static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
   return GM_OK;
 }
 
+// Elements per chunk of a long row: about six units per CTA of the persistent
+// grid if the batch were all long rows (so the last wave of units leaves few SMs
+// idle), whole pre-pass pieces, between 2 pieces and SPLIT_LEN.
+static int chunk_len_for(int64_t nnz, int grid) {
+  int64_t c = nnz / ((int64_t)(grid > 0 ? grid : 1) * 6);
+  c = c / PIECE_LEN * PIECE_LEN;
+  if (c < 2 * PIECE_LEN) c = 2 * PIECE_LEN;
+  if (c > SPLIT_LEN) c = SPLIT_LEN;
+  return (int)c;
+}
+
 template <int ARITH>
-static int launch_all(const SketchArgs& a, bool plain, int nsm, cudaStream_t stream) {
+static int launch_all(SketchArgs a, bool plain, int nsm, cudaStream_t stream) {
   const size_t sm = plain ? plain_smem_bytes(a.k) : fast_smem_bytes(a.k, a.ndense);
-  const int max_units = a.n_rows + (int)((a.nnz + SPLIT_LEN - 1) / SPLIT_LEN);
-  plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);
-  longprep_kernel<<<nsm * 4, 256, 0, stream>>>(a);
   int grid = 0, rc;
+  {
+    int per_sm = 0;
+    const void* kern = plain ? (const void*)plain_kernel<ARITH> : (const void*)fastgm_kernel<ARITH, MODE_MAIN>;
+    if (allow_max_smem(kern) != GM_OK) return GM_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, sm) != cudaSuccess) return GM_ECUDA;
+    a.chunk_len = chunk_len_for(a.nnz, nsm * (per_sm > 0 ? per_sm : 1));
+  }
+  const int max_units = a.n_rows + (int)((a.nnz + a.chunk_len - 1) / a.chunk_len) + a.max_long;
+  plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);
+  longprep_kernel<<<nsm * 8, PREP_THREADS, 0, stream>>>(a);
   if (plain) {
     if constexpr (BLOCK != 512) {
       return GM_EINVAL;  // the plain sketch runs with 512-thread CTAs only
@@ -648,8 +684,10 @@ static int launch_all(const SketchArgs& a, bool plain, int nsm, cudaStream_t str
   if (g_main_before) cudaEventRecord(g_main_before, stream);
   fastgm_kernel<ARITH, MODE_MAIN><<<grid, BLOCK, sm, stream>>>(a);
   if (g_main_after) cudaEventRecord(g_main_after, stream);
+  // the redo kernel: long rows left unfilled are rare (p = 1e-3 per row), so a
+  // small grid; its empty launch then costs little
   int grid_esc = 0;
-  rc = occupancy_grid(fastgm_kernel<ARITH, MODE_ESC>, sm, nsm, a.max_long, grid_esc);
+  rc = occupancy_grid(fastgm_kernel<ARITH, MODE_ESC>, sm, nsm, a.max_long < 16 ? a.max_long : 16, grid_esc);
   if (rc != GM_OK) return rc;
   fastgm_kernel<ARITH, MODE_ESC><<<grid_esc, BLOCK, sm, stream>>>(a);
   return GM_OK;

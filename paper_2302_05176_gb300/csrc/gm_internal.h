@@ -14,7 +14,8 @@ namespace gm {
 constexpr int WS_NCOUNTERS = 16;
 constexpr uint32_t WS_EDATA = 1u;
 constexpr uint32_t WS_ETIMEOUT = 2u;
-constexpr int SPLIT_LEN = 32768;  // rows longer than this are cut into chunks of this many elements
+constexpr int SPLIT_LEN = 32768;  // rows longer than this are long rows, cut into chunks
+constexpr int PIECE_LEN = 4096;   // long rows' pre-pass pieces (one warp each); chunks are whole pieces
 
 // Start of every workspace; zeroed by the first kernel of each call.
 struct WsHeader {
@@ -24,19 +25,33 @@ struct WsHeader {
   uint32_t n_extra;       // chunk units of long rows beyond their first chunk
   uint32_t esc_count;     // long rows to redo with a larger bound
   uint32_t esc_counter;   // next entry of that list
-  uint32_t pad[2];
+  uint32_t n_pieces;      // pre-pass pieces of all long rows
+  uint32_t pad;
   unsigned long long counters[WS_NCOUNTERS];
 };
 
 // Per long row: its row index, chunk count, first extra unit, sum of weights.
+// The sums are added from the row's pre-pass pieces in piece order, so they are
+// the same bits on every call.
 struct LongRow {
   uint32_t row;
   uint32_t nchunks;
-  uint32_t chunk_off;  // index of its first extra unit (chunks 1 .. nchunks-1)
-  uint32_t done;       // chunks finished
-  float sum;           // sum of positive weights (FP32, places the bound only)
-  int npos;            // positive weights
-  double dsum;         // FP64 sum of the positive weights (budget passes only)
+  uint32_t chunk_off;    // index of its first extra unit (chunks 1 .. nchunks-1)
+  uint32_t done;         // chunks finished
+  float sum;             // sum of positive weights (FP32, places the bound only)
+  int npos;              // positive weights
+  double dsum;           // FP64 sum of the positive weights (budget passes only)
+  uint32_t piece_off;    // index of its first pre-pass piece
+  uint32_t npieces;      // pieces of PIECE_LEN elements
+  uint32_t pieces_done;  // pieces summed so far
+  uint32_t pad;
+};
+
+// Sums of one pre-pass piece of a long row.
+struct LongPiece {
+  float sum;
+  int npos;
+  double dsum;
 };
 
 constexpr size_t WS_HEADER_BYTES = 256;
@@ -44,10 +59,12 @@ constexpr size_t WS_HEADER_BYTES = 256;
 constexpr size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 constexpr int64_t max_long_rows(int64_t nnz) { return nnz / (SPLIT_LEN + 1) + 1; }
+constexpr int64_t max_pieces(int64_t nnz) { return nnz / PIECE_LEN + max_long_rows(nnz) + 1; }
 
 // Workspace: header | C table (k doubles) | work list (nnz u32) | promotion list
 // (nnz u32) | long index per row (n_rows i32) | long rows (max_long) | long
-// registers (max_long * k * 16 B) | escalation list (max_long u32)
+// registers (max_long * k * 16 B) | escalation list (max_long u32) | piece sums
+// (max_pieces)
 struct WsLayout {
   WsHeader* hdr;
   double* ctab;
@@ -57,6 +74,7 @@ struct WsLayout {
   LongRow* longs;
   void* long_regs;
   uint32_t* esc;
+  LongPiece* parts;
   int64_t max_long;
 };
 
@@ -80,6 +98,8 @@ inline WsLayout ws_layout(void* ws, int32_t n_rows, int64_t nnz, int k) {
   L.long_regs = p + off;
   off += round_up((size_t)ml * (size_t)k * 16, 256);
   L.esc = reinterpret_cast<uint32_t*>(p + off);
+  off += round_up((size_t)ml * 4, 256);
+  L.parts = reinterpret_cast<LongPiece*>(p + off);
   L.max_long = ml;
   return L;
 }
@@ -87,7 +107,8 @@ inline WsLayout ws_layout(void* ws, int32_t n_rows, int64_t nnz, int k) {
 constexpr size_t ws_bytes(int32_t n_rows, int64_t nnz, int k) {
   return WS_HEADER_BYTES + round_up((size_t)k * 8, 256) + 2 * round_up((size_t)nnz * 4, 256) +
          round_up((size_t)n_rows * 4, 256) + round_up((size_t)max_long_rows(nnz) * sizeof(LongRow), 256) +
-         round_up((size_t)max_long_rows(nnz) * (size_t)k * 16, 256) + round_up((size_t)max_long_rows(nnz) * 4, 256);
+         round_up((size_t)max_long_rows(nnz) * (size_t)k * 16, 256) + round_up((size_t)max_long_rows(nnz) * 4, 256) +
+         round_up((size_t)max_pieces(nnz) * sizeof(LongPiece), 256);
 }
 
 // Caller workspaces start on a 256-byte boundary (every region inside is laid
@@ -100,6 +121,11 @@ inline bool ws_aligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) &
 int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
                   int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
                   size_t workspace_bytes, cudaStream_t stream, bool plain, const float* t_row);
+
+// Events that gm_diag_time_aux_kernels registered (null when unset): the estimator
+// and learned pre-pass entry points record them before their first and after their
+// last kernel.
+void aux_events(cudaEvent_t* before, cudaEvent_t* after);
 
 // Entries per dense permutation: k rounded up to a multiple of 8, so that each
 // array starts on a 16-byte boundary (16-byte stores).

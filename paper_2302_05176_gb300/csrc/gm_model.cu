@@ -1018,7 +1018,13 @@ extern "C" int gm_learned_bound(const int64_t* row_ptr, const double* w, int32_t
     return GM_EINVAL;
   if (workspace_bytes < learned_ws_bytes(n_rows, nnz)) return GM_ENOMEM;
   const gm::TraceRange trace("gm_learned_bound");
-  return learned_bound_launch(row_ptr, w, n_rows, nnz, k, params, margin, t_out, workspace, (cudaStream_t)stream);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  aux_events(&ev0, &ev1);
+  if (ev0) cudaEventRecord(ev0, (cudaStream_t)stream);
+  const int rc =
+      learned_bound_launch(row_ptr, w, n_rows, nnz, k, params, margin, t_out, workspace, (cudaStream_t)stream);
+  if (ev1) cudaEventRecord(ev1, (cudaStream_t)stream);
+  return rc;
 }
 
 extern "C" size_t gm_sketch_learned_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k) {

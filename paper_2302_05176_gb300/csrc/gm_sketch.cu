@@ -57,6 +57,11 @@ namespace gm {
 #ifndef GM_MED_SW
 #define GM_MED_SW 8
 #endif
+// 1: a warp's next screening batch is claimed and its loads issued while the
+// current one is screened; 0: loaded when it is screened (weight and id together)
+#ifndef GM_SCREEN_PREFETCH
+#define GM_SCREEN_PREFETCH 1
+#endif
 // Default routing by the expected number of arrivals below T (gm_tuning): light
 // lanes up to LIGHT_MAX, 8-lane segments up to MEDIUM_MAX, 32-lane warps up to
 // HEAVY_MAX, dense permutations beyond; first-pass bound at quantile 1 - P_FIRST.
@@ -101,6 +106,8 @@ struct SketchArgs {
   Reg* long_regs;
   uint32_t* esc;
   int max_long;
+  LongPiece* parts;       // per pre-pass piece of the long rows: its sums
+  int chunk_len;          // elements per chunk of a long row (a multiple of PIECE_LEN, <= SPLIT_LEN)
   int ndense;             // dense permutations per CTA (warps that take super-heavy elements)
   float q1, q2, q_split;  // normalised bounds: first pass, second pass, long rows (inf = none)
   float grow;             // factor of each later pass's bound over the one before (a power of two)
@@ -295,9 +302,10 @@ __device__ __forceinline__ void block_sum(const SketchArgs& a, int64_t lo, int n
   __syncthreads();
 }
 
-// 128-bit compare-and-swap minimum on a global register (the union of Sec. 2.3).
-__device__ __forceinline__ void global_lower(Reg* r, uint64_t yb, uint64_t id, bool& gave_up) {
-  uint64_t cy = __ldcg(&r->y), cid = __ldcg(&r->id);
+// 128-bit compare-and-swap minimum on a global register (the union of Sec. 2.3),
+// starting from (cy, cid), a value the register held at some point.
+__device__ __forceinline__ void global_lower_from(Reg* r, uint64_t yb, uint64_t id, uint64_t cy, uint64_t cid,
+                                                  bool& gave_up) {
   int tries = 0;
   while (yb < cy || (yb == cy && id < cid)) {
     uint64_t oy, oid;
@@ -316,6 +324,37 @@ __device__ __forceinline__ void global_lower(Reg* r, uint64_t yb, uint64_t id, b
     if (++tries >= CAS_CAP) {
       gave_up = true;
       break;
+    }
+  }
+}
+
+__device__ __forceinline__ void global_lower(Reg* r, uint64_t yb, uint64_t id, bool& gave_up) {
+  global_lower_from(r, yb, id, __ldcg(&r->y), __ldcg(&r->id), gave_up);
+}
+
+// Merge a unit's k shared registers into the row's global ones, every filled
+// register by the 128-bit minimum; each thread first loads the current values of
+// up to four of its global registers at once, so their latencies overlap.
+template <int NT>
+__device__ __forceinline__ void merge_to_global(const Reg* regs, Reg* g, int k, bool& gave_up) {
+  for (int j0 = threadIdx.x; j0 < k; j0 += 4 * NT) {
+    uint64_t cy[4], cid[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + q * NT;
+      cy[q] = cid[q] = 0ull;
+      if (j < k) {
+        cy[q] = __ldcg(&g[j].y);
+        cid[q] = __ldcg(&g[j].id);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + q * NT;
+      if (j < k) {
+        const Reg r = regs[j];
+        if (r.y != INF_BITS) global_lower_from(&g[j], r.y, r.id, cy[q], cid[q], gave_up);
+      }
     }
   }
 }
@@ -359,12 +398,35 @@ __global__ void init_kernel(WsHeader* hdr, double* ctab, int k, const int64_t* r
   }
 }
 
-// Find the long rows, number their extra chunks (one CTA of 1024 threads).
+// Find the long rows, number their extra chunks and their pre-pass pieces (one
+// CTA of 1024 threads).
 constexpr int PLAN_THREADS = 1024;
+
+// Exclusive scan of x over the CTA in blocks of PLAN_THREADS, `carry` the running
+// total (shared); returns this thread's offset.  Block-wide.
+__device__ __forceinline__ uint32_t plan_scan(uint32_t x, uint32_t* part, uint32_t& carry) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) part[warp] = incl;
+  __syncthreads();
+  uint32_t wofs = 0u;
+  for (int q = 0; q < warp; ++q) wofs += part[q];
+  const uint32_t off = carry + wofs + incl - x;
+  __syncthreads();
+  if (tid == PLAN_THREADS - 1) carry += wofs + incl;
+  __syncthreads();
+  return off;
+}
+
 __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(SketchArgs a) {
   __shared__ uint32_t part[PLAN_THREADS / 32];
-  __shared__ uint32_t carry;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ uint32_t carry_c, carry_p;
+  const int tid = threadIdx.x;
   for (int r = tid; r < a.n_rows; r += PLAN_THREADS) {
     int64_t lo, hi;
     row_bounds(a, r, lo, hi);
@@ -376,12 +438,16 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(SketchArgs a) {
         li = (int32_t)i;
         LongRow lr;
         lr.row = (uint32_t)r;
-        lr.nchunks = (uint32_t)((len + SPLIT_LEN - 1) / SPLIT_LEN);
+        lr.nchunks = (uint32_t)((len + a.chunk_len - 1) / a.chunk_len);
         lr.chunk_off = 0u;
         lr.done = 0u;
         lr.sum = 0.0f;
         lr.npos = 0;
         lr.dsum = 0.0;
+        lr.piece_off = 0u;
+        lr.npieces = (uint32_t)((len + PIECE_LEN - 1) / PIECE_LEN);
+        lr.pieces_done = 0u;
+        lr.pad = 0u;
         a.longs[i] = lr;
       }
     }
@@ -389,40 +455,38 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(SketchArgs a) {
   }
   __syncthreads();
   if (tid == 0) {
-    carry = 0u;
+    carry_c = carry_p = 0u;
     if ((int)a.hdr->n_long > a.max_long) a.hdr->n_long = (uint32_t)a.max_long;  // cannot happen: max_long bounds it
   }
   __syncthreads();
   const uint32_t n_long = a.hdr->n_long;
-  for (uint32_t base = 0; base < n_long; base += PLAN_THREADS) {  // exclusive scan of (nchunks - 1)
+  for (uint32_t base = 0; base < n_long; base += PLAN_THREADS) {  // exclusive scans of (nchunks - 1), npieces
     const uint32_t i = base + tid;
-    const uint32_t x = i < n_long ? a.longs[i].nchunks - 1u : 0u;
-    uint32_t incl = x;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, incl, d);
-      if (lane >= d) incl += y;
+    const uint32_t xc = i < n_long ? a.longs[i].nchunks - 1u : 0u;
+    const uint32_t xp = i < n_long ? a.longs[i].npieces : 0u;
+    const uint32_t oc = plan_scan(xc, part, carry_c);
+    const uint32_t op = plan_scan(xp, part, carry_p);
+    if (i < n_long) {
+      a.longs[i].chunk_off = oc;
+      a.longs[i].piece_off = op;
     }
-    if (lane == 31) part[warp] = incl;
-    __syncthreads();
-    uint32_t wofs = 0u;
-    for (int q = 0; q < warp; ++q) wofs += part[q];
-    if (i < n_long) a.longs[i].chunk_off = carry + wofs + incl - x;
-    __syncthreads();
-    if (tid == PLAN_THREADS - 1) carry += wofs + incl;
-    __syncthreads();
   }
-  if (tid == 0) a.hdr->n_extra = carry;
+  if (tid == 0) {
+    a.hdr->n_extra = carry_c;
+    a.hdr->n_pieces = carry_p;
+  }
 }
 
-// Sums of the long rows (FP32, they place the bound) and their global registers
-// set to unfilled.  Grid-stride over all chunks of all long rows.
-__global__ void __launch_bounds__(256) longprep_kernel(SketchArgs a) {
-  __shared__ float red_f[8];
-  __shared__ int red_i[8];
-  __shared__ double red_d[8];
-  const uint32_t n_long = a.hdr->n_long, n_extra = a.hdr->n_extra;
-  const uint32_t n_chunks = n_long + n_extra;
+// Long rows: their global registers set to unfilled (or to the running sketch),
+// and the sums of their weights.  One warp per pre-pass piece of PIECE_LEN
+// elements: lane l adds elements l, l + 32, ... (FP32 Kahan sum built from the
+// bits, the count, the FP64 sum for budget passes; GM_FLAG_VALIDATE's checks),
+// the lanes combine in a fixed butterfly, the piece's sums go to parts[], and the
+// warp that finishes a row's last piece adds its pieces in piece order.  So the
+// sums are the same bits on every call, whatever the scheduling.
+constexpr int PREP_THREADS = 256;
+__global__ void __launch_bounds__(PREP_THREADS) longprep_kernel(SketchArgs a) {
+  const uint32_t n_long = a.hdr->n_long, n_pieces = a.hdr->n_pieces;
   const int k = a.k;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < (int64_t)n_long * k;
        j += (int64_t)gridDim.x * blockDim.x) {
@@ -435,33 +499,81 @@ __global__ void __launch_bounds__(256) longprep_kernel(SketchArgs a) {
       a.long_regs[j].id = UNFILLED_ID;
     }
   }
-  // SUB pieces per chunk, so that enough CTAs stream each long row
-  constexpr int SUB = 8, PIECE = SPLIT_LEN / SUB;
-  for (uint32_t cs = blockIdx.x; cs < n_chunks * SUB; cs += gridDim.x) {
-    // chunk c: the first chunk of long row c (c < n_long) or extra unit c - n_long
-    const uint32_t c = cs / SUB, piece = cs % SUB;
-    int row, chunk, longi;
-    if (c < n_long) {
-      longi = (int)c;
-      row = (int)a.longs[c].row;
-      chunk = 0;
-    } else {
-      resolve_unit(a, c - n_long, n_extra, n_long, row, chunk, longi);
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (PREP_THREADS / 32);
+  for (uint32_t p = blockIdx.x * (PREP_THREADS / 32) + (threadIdx.x >> 5); p < n_pieces; p += warps) {
+    int lo_i = 0, hi_i = (int)n_long - 1;  // the long row owning piece p
+    while (lo_i < hi_i) {
+      const int mid = (lo_i + hi_i + 1) >> 1;
+      if (a.longs[mid].piece_off <= p)
+        lo_i = mid;
+      else
+        hi_i = mid - 1;
     }
+    const int li = lo_i;
     int64_t lo, hi;
-    row_bounds(a, row, lo, hi);
-    const int64_t clo = lo + (int64_t)chunk * SPLIT_LEN + (int64_t)piece * PIECE;
-    const int64_t chi = min(hi, clo + PIECE);
-    if (chi <= clo) continue;  // uniform over the block
-    float s;
-    int np;
-    block_sum<256>(a, clo, (int)(chi - clo), red_f, red_i, s, np);
+    row_bounds(a, (int)a.longs[li].row, lo, hi);
+    const int64_t plo = lo + (int64_t)(p - a.longs[li].piece_off) * PIECE_LEN;
+    const int n = (int)min((int64_t)PIECE_LEN, hi - plo);
+    float s = 0.0f, comp = 0.0f;
     double ds = 0.0;
-    if (a.r_row) ds = block_dsum<256>(a.w, clo, (int)(chi - clo), red_d);
-    if (threadIdx.x == 0) {
-      atomicAdd(&a.longs[longi].sum, s);
-      atomicAdd(&a.longs[longi].npos, np);
-      if (a.r_row) atomicAdd(&a.longs[longi].dsum, ds);
+    int c = 0;
+    bool bad = false;
+#pragma unroll 8
+    for (int i = lane; i < n; i += 32) {
+      const double v = __ldcs(a.w + plo + i);
+      if (positive_finite(v)) {
+        const float y = f32_trunc(v) - comp;
+        const float t = s + y;
+        comp = (t - s) - y;
+        s = t;
+        ds += v;
+        ++c;
+      } else if (a.flags & GM_FLAG_VALIDATE) {
+        const uint64_t b = (uint64_t)__double_as_longlong(v);
+        if ((b << 1) != 0ull) bad = true;  // neither +0 nor -0: negative, NaN or inf
+      }
+      if ((a.flags & GM_FLAG_VALIDATE) && a.ids[plo + i] < 0) bad = true;
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(&a.hdr->status, WS_EDATA);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      s += __shfl_xor_sync(FULL, s, d);
+      ds += __shfl_xor_sync(FULL, ds, d);
+      c += __shfl_xor_sync(FULL, c, d);
+    }
+    unsigned int last = 0u;
+    if (lane == 0) {
+      a.parts[p] = LongPiece{s, c, ds};
+      __threadfence();
+      last = (atomicAdd(&a.longs[li].pieces_done, 1u) == a.longs[li].npieces - 1u) ? 1u : 0u;
+    }
+    if (__shfl_sync(FULL, last, 0)) {  // the row's last piece: add its pieces in order
+      __threadfence();
+      const uint32_t p0 = a.longs[li].piece_off, np = a.longs[li].npieces;
+      float rs = 0.0f, rc = 0.0f;
+      double rd = 0.0;
+      int rn = 0;
+      for (uint32_t q = lane; q < np; q += 32) {
+        const LongPiece* pp = a.parts + p0 + q;
+        const float y = __ldcg(&pp->sum) - rc;
+        const float t = rs + y;
+        rc = (t - rs) - y;
+        rs = t;
+        rd += __ldcg(&pp->dsum);
+        rn += __ldcg(&pp->npos);
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        rs += __shfl_xor_sync(FULL, rs, d);
+        rd += __shfl_xor_sync(FULL, rd, d);
+        rn += __shfl_xor_sync(FULL, rn, d);
+      }
+      if (lane == 0) {
+        a.longs[li].sum = rs;
+        a.longs[li].dsum = rd;
+        a.longs[li].npos = rn;
+      }
     }
   }
 }
@@ -606,6 +718,8 @@ static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const
   a.longs = L.longs;
   a.long_regs = reinterpret_cast<Reg*>(L.long_regs);
   a.esc = L.esc;
+  a.parts = L.parts;
+  a.chunk_len = SPLIT_LEN;  // set per shape by the launcher
   a.max_long = (int)L.max_long;
   a.t_row = plain ? nullptr : t_row;
   a.init_s = init_s;
@@ -995,9 +1109,9 @@ extern "C" int gm_row_ystar(const double* y, int32_t n_rows, int32_t k, double* 
 namespace gm {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = ws_bytes(GM_NOALLOC_MAX_ROWS, GM_NOALLOC_MAX_NNZ, GM_MAX_K);
-// 10,782,208 bytes (about 10.8 MB, 10.3 MiB): two 4 MiB element lists, 2 MiB of
+// 10,787,584 bytes (about 10.8 MB, 10.3 MiB): two 4 MiB element lists, 2 MiB of
 // long-row registers, the per-row index and the small tables.
-static_assert(NOALLOC_SCRATCH_BYTES == 10782208, "the documented size of the no-alloc scratch changed");
+static_assert(NOALLOC_SCRATCH_BYTES == 10787584, "the documented size of the no-alloc scratch changed");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 

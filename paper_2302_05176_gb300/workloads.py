@@ -198,7 +198,7 @@ def _progression_ids(rng, n, space=ID_SPACE):
 
 def serving_requests(seed=1, n_requests=2000, rate=20_000.0, n_lo=100, n_hi=5_000_000,
                      ks=(256, 1024, 4096), query_frac=0.3, pair_frac=0.5, shared=0.5, sigma=0.2,
-                     max_nnz=None):
+                     max_nnz=None, n_vectors=None):
     """A Poisson stream of sketch requests plus Jaccard / cardinality queries.
 
     Sketch sizes n+ are log-uniform in [n_lo, n_hi], weights Exp(1) or
@@ -207,12 +207,16 @@ def serving_requests(seed=1, n_requests=2000, rate=20_000.0, n_lo=100, n_hi=5_00
     keep ``shared`` of its ids with the weights multiplied by exp(N(0, sigma^2)),
     add fresh ids for the rest, and use its k; the Jaccard queries are over such
     pairs, the cardinality queries over any earlier sketch.  Queries refer to
-    sketch requests by their index in the stream.  ``max_nnz`` caps n+.
+    sketch requests by their index in the stream.  ``max_nnz`` caps n+.  With
+    ``n_vectors``, once that many distinct vectors exist every later sketch
+    request sketches one of them again (chosen uniformly, k drawn afresh), so a
+    long stream needs only that many vectors in host memory.
     """
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
     hi = n_hi if max_nnz is None else min(n_hi, max_nnz)
     reqs, sketch_idx, pairs = [], [], []
+    distinct = []
     for q in range(n_requests):
         if sketch_idx and rng.random() < query_frac:
             if pairs and rng.random() < 0.5:
@@ -221,6 +225,11 @@ def serving_requests(seed=1, n_requests=2000, rate=20_000.0, n_lo=100, n_hi=5_00
             else:
                 h = int(rng.choice(sketch_idx))
                 reqs.append(Request(float(t[q]), "cardinality", reqs[h].k, handle=h))
+            continue
+        if n_vectors is not None and len(distinct) >= n_vectors:
+            a = distinct[int(rng.integers(len(distinct)))]
+            reqs.append(Request(float(t[q]), "sketch", int(rng.choice(ks)), csr=reqs[a].csr))
+            sketch_idx.append(q)
             continue
         if sketch_idx and rng.random() < pair_frac:
             a = int(rng.choice(sketch_idx))
@@ -242,6 +251,7 @@ def serving_requests(seed=1, n_requests=2000, rate=20_000.0, n_lo=100, n_hi=5_00
                                                                        ids.astype(np.int32), w)))
             pairs.append((a, q))
             sketch_idx.append(q)
+            distinct.append(q)
             continue
         n = int(np.exp(rng.uniform(np.log(n_lo), np.log(hi))))
         ids = _progression_ids(rng, n)
@@ -249,4 +259,5 @@ def serving_requests(seed=1, n_requests=2000, rate=20_000.0, n_lo=100, n_hi=5_00
         k = int(rng.choice(ks))
         reqs.append(Request(float(t[q]), "sketch", k, csr=CSR(np.array([0, n], dtype=np.int64), ids, w)))
         sketch_idx.append(q)
+        distinct.append(q)
     return reqs
