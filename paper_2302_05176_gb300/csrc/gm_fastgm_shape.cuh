@@ -43,7 +43,10 @@ __host__ __device__ inline size_t plain_smem_bytes(int k) {
 // as an FP32 value (equal as reals).  Elements expected to need more than
 // a.light_max arrivals go to the work list, tagged by their expected count.
 // --------------------------------------------------------------------------
-template <int ARITH>
+// PF: claim and load each screening batch one batch ahead (long-row chunks, whose
+// elements come from HBM); without it a batch is loaded when it is screened
+// (short rows, whose weights the row sum has just brought into L2).
+template <int ARITH, bool PF>
 __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int n, uint64_t Tbits, float Tf,
                                             Reg* regs, uint32_t* map, unsigned char* wbuf, SmemScalars& sh,
                                             Counters& cnt, bool& gave_up) {
@@ -64,27 +67,27 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
   int nbase = 0;
   double nv = 0.0;
   int32_t nid = 0;
-#if GM_SCREEN_PREFETCH
-  if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
-  nbase = __shfl_sync(FULL, nbase, 0);
-  if (nbase + lane < n) {
-    nv = __ldcs(a.w + lo + nbase + lane);
-    nid = __ldcs(a.ids + lo + nbase + lane);
+  if (PF) {
+    if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
+    nbase = __shfl_sync(FULL, nbase, 0);
+    if (nbase + lane < n) {
+      nv = __ldcs(a.w + lo + nbase + lane);
+      nid = __ldcs(a.ids + lo + nbase + lane);
+    }
   }
-#endif
   while (true) {
     // hand survivors to idle lanes, screening new elements while some are idle
     uint32_t nmask = __ballot_sync(FULL, e < 0);
     while (nmask && !(pool_done && wcount == 0)) {
       if (wcount == 0) {
-#if !GM_SCREEN_PREFETCH
-        if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
-        nbase = __shfl_sync(FULL, nbase, 0);
-        if (nbase + lane < n) {
-          nv = a.w[lo + nbase + lane];
-          nid = a.ids[lo + nbase + lane];
+        if (!PF) {
+          if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
+          nbase = __shfl_sync(FULL, nbase, 0);
+          if (nbase + lane < n) {
+            nv = a.w[lo + nbase + lane];
+            nid = a.ids[lo + nbase + lane];
+          }
         }
-#endif
         const int base = nbase;
         if (base >= n) {
           pool_done = true;
@@ -94,14 +97,14 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
         bool surv = false;
         double v = nv;
         int32_t idv = nid;
-#if GM_SCREEN_PREFETCH
-        if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
-        nbase = __shfl_sync(FULL, nbase, 0);
-        if (nbase + lane < n) {
-          nv = __ldcs(a.w + lo + nbase + lane);
-          nid = __ldcs(a.ids + lo + nbase + lane);
+        if (PF) {
+          if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
+          nbase = __shfl_sync(FULL, nbase, 0);
+          if (nbase + lane < n) {
+            nv = __ldcs(a.w + lo + nbase + lane);
+            nid = __ldcs(a.ids + lo + nbase + lane);
+          }
         }
-#endif
         if (slot < n) {
           if (positive_finite(v)) {
             ++cnt.elements;
@@ -344,7 +347,8 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
     reset_lists(sh);
     __syncthreads();
     clk_add(cnt, CLK_SETUP, t);
-    light_phase<ARITH>(a, lo, n, Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt, gave_up);
+    light_phase<ARITH, false>(a, lo, n, Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt,
+                              gave_up);
     clk_add(cnt, CLK_LIGHT, t);
     __syncthreads();
     clk_add(cnt, CLK_WAIT, t);
@@ -430,6 +434,53 @@ __device__ __forceinline__ bool ladder_bound(const Reg* g, int k, float sumc, in
   return final;
 }
 
+// One chunk of a long row: its elements with the bound from the row's sum (or,
+// in the bound-free mode, a ladder of passes on the chunk's own registers), then
+// its registers merged into the row's global ones.
+template <int ARITH>
+__device__ __forceinline__
+void chunk_unit(const SketchArgs& a, int row, int chunk, int longi, int64_t lo, int64_t hi, Reg* regs,
+                uint32_t* area, uint16_t* dense, unsigned char* wbuf, SmemScalars& sh, Counters& cnt,
+                bool& gave_up) {
+  const int k = a.k, tid = threadIdx.x;
+  const int64_t clo = lo + (int64_t)chunk * a.chunk_len;
+  const int64_t chi = min(hi, clo + a.chunk_len);
+  Reg* g = a.long_regs + (int64_t)longi * k;
+  if (chi > clo) {
+    float tdummy;
+    const bool ladder = a.chunk_ladder && !row_bound(a, row, tdummy);
+    float sumc = 0.0f;
+    int nposc = 1;
+    long long t = read_clock();
+    if (ladder) block_sum<BLOCK>(a, clo, (int)(chi - clo), sh.red_f, sh.red_i, sumc, nposc);
+    for (int pass = 0; nposc > 0; ++pass) {
+      uint64_t Tbits;
+      float Tf;
+      bool final = true;
+      if (ladder)
+        final = ladder_bound(g, k, sumc, pass, sh, Tbits, Tf);
+      else
+        chunk_bound(a, row, a.longs[longi].sum, Tbits, Tf);
+      reset_lists(sh);
+      __syncthreads();
+      clk_add(cnt, CLK_SETUP, t);
+      light_phase<ARITH, true>(a, clo, (int)(chi - clo), Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh,
+                               cnt, gave_up);
+      clk_add(cnt, CLK_LIGHT, t);
+      __syncthreads();
+      clk_add(cnt, CLK_WAIT, t);
+      warp_phases<ARITH>(a, clo, (int)(chi - clo), Tbits, regs, area, dense, sh, cnt, gave_up, t);
+      if (final) break;
+      // the chunk's own sketch is exact once its registers are all at or below T
+      int empty = 0;
+      for (int j = tid; j < k; j += BLOCK) empty |= (regs[j].y > Tbits);
+      if (!__syncthreads_or(empty)) break;
+      if (tid == 0) ++cnt.escalated;
+    }
+    merge_to_global<BLOCK>(regs, g, k, gave_up);
+  }
+}
+
 template <int ARITH, int MODE>
 __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -471,45 +522,8 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
       __syncthreads();
       continue;
     }
-    // one chunk of a long row, bound from the row's sum (rowsum kernel); in the
-    // bound-free mode a ladder of passes on the chunk's own registers instead
-    const int64_t clo = lo + (int64_t)chunk * a.chunk_len;
-    const int64_t chi = min(hi, clo + a.chunk_len);
     const LongRow lr = a.longs[longi];
-    Reg* g = a.long_regs + (int64_t)longi * k;
-    if (lr.npos > 0 && chi > clo) {
-      float tdummy;
-      const bool ladder = a.chunk_ladder && !row_bound(a, row, tdummy);
-      float sumc = 0.0f;
-      int nposc = 1;
-      long long t = read_clock();
-      if (ladder) block_sum<BLOCK>(a, clo, (int)(chi - clo), sh.red_f, sh.red_i, sumc, nposc);
-      for (int pass = 0; nposc > 0; ++pass) {
-        uint64_t Tbits;
-        float Tf;
-        bool final = true;
-        if (ladder)
-          final = ladder_bound(g, k, sumc, pass, sh, Tbits, Tf);
-        else
-          chunk_bound(a, row, lr.sum, Tbits, Tf);
-        reset_lists(sh);
-        __syncthreads();
-        clk_add(cnt, CLK_SETUP, t);
-        light_phase<ARITH>(a, clo, (int)(chi - clo), Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh,
-                           cnt, gave_up);
-        clk_add(cnt, CLK_LIGHT, t);
-        __syncthreads();
-        clk_add(cnt, CLK_WAIT, t);
-        warp_phases<ARITH>(a, clo, (int)(chi - clo), Tbits, regs, area, dense, sh, cnt, gave_up, t);
-        if (final) break;
-        // the chunk's own sketch is exact once its registers are all at or below T
-        int empty = 0;
-        for (int j = tid; j < k; j += BLOCK) empty |= (regs[j].y > Tbits);
-        if (!__syncthreads_or(empty)) break;
-        if (tid == 0) ++cnt.escalated;
-      }
-      merge_to_global<BLOCK>(regs, g, k, gave_up);
-    }
+    if (lr.npos > 0) chunk_unit<ARITH>(a, row, chunk, longi, lo, hi, regs, area, dense, wbuf, sh, cnt, gave_up);
     __threadfence();
     __syncthreads();
     if (tid == 0) sh.last = (atomicAdd(&a.longs[longi].done, 1u) == lr.nchunks - 1) ? 1 : 0;
@@ -642,11 +656,14 @@ static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
   return GM_OK;
 }
 
-// Elements per chunk of a long row: about six units per CTA of the persistent
-// grid if the batch were all long rows (so the last wave of units leaves few SMs
-// idle), whole pre-pass pieces, between 2 pieces and SPLIT_LEN.
+// Elements per chunk of a long row: SPLIT_LEN, or (GM_CHUNK_UNITS_PER_CTA > 0)
+// about that many units per CTA of the persistent grid if the batch were all
+// long rows, whole pre-pass pieces, between 2 pieces and SPLIT_LEN.  (Measured:
+// 16,384-element chunks made the 16 x 10^6 Pareto launch slower, 0.478 against
+// 0.40 ms: each unit's phase barriers and merge cost more than the balance gained.)
 static int chunk_len_for(int64_t nnz, int grid) {
-  int64_t c = nnz / ((int64_t)(grid > 0 ? grid : 1) * 6);
+  if (GM_CHUNK_UNITS_PER_CTA <= 0) return SPLIT_LEN;
+  int64_t c = nnz / ((int64_t)(grid > 0 ? grid : 1) * GM_CHUNK_UNITS_PER_CTA);
   c = c / PIECE_LEN * PIECE_LEN;
   if (c < 2 * PIECE_LEN) c = 2 * PIECE_LEN;
   if (c > SPLIT_LEN) c = SPLIT_LEN;

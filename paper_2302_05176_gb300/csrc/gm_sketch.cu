@@ -57,10 +57,9 @@ namespace gm {
 #ifndef GM_MED_SW
 #define GM_MED_SW 8
 #endif
-// 1: a warp's next screening batch is claimed and its loads issued while the
-// current one is screened; 0: loaded when it is screened (weight and id together)
-#ifndef GM_SCREEN_PREFETCH
-#define GM_SCREEN_PREFETCH 1
+// Long-row chunk length policy (see chunk_len_for): 0 = SPLIT_LEN.
+#ifndef GM_CHUNK_UNITS_PER_CTA
+#define GM_CHUNK_UNITS_PER_CTA 0
 #endif
 // Default routing by the expected number of arrivals below T (gm_tuning): light
 // lanes up to LIGHT_MAX, 8-lane segments up to MEDIUM_MAX, 32-lane warps up to
@@ -519,21 +518,35 @@ __global__ void __launch_bounds__(PREP_THREADS) longprep_kernel(SketchArgs a) {
     double ds = 0.0;
     int c = 0;
     bool bad = false;
-#pragma unroll 8
-    for (int i = lane; i < n; i += 32) {
-      const double v = __ldcs(a.w + plo + i);
-      if (positive_finite(v)) {
-        const float y = f32_trunc(v) - comp;
-        const float t = s + y;
-        comp = (t - s) - y;
-        s = t;
-        ds += v;
-        ++c;
-      } else if (a.flags & GM_FLAG_VALIDATE) {
-        const uint64_t b = (uint64_t)__double_as_longlong(v);
-        if ((b << 1) != 0ull) bad = true;  // neither +0 nor -0: negative, NaN or inf
+    const bool validate = (a.flags & GM_FLAG_VALIDATE) != 0;
+    for (int base = 0; base < n; base += 32 * 8) {  // eight loads in flight per lane, then their sums
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int i = base + q * 32 + lane;
+        v[q] = i < n ? __ldcs(a.w + plo + i) : 0.0;
       }
-      if ((a.flags & GM_FLAG_VALIDATE) && a.ids[plo + i] < 0) bad = true;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (positive_finite(v[q])) {
+          const float y = f32_trunc(v[q]) - comp;
+          const float t = s + y;
+          comp = (t - s) - y;
+          s = t;
+          ds += v[q];
+          ++c;
+        } else if (validate) {
+          const uint64_t b = (uint64_t)__double_as_longlong(v[q]);
+          if ((b << 1) != 0ull) bad = true;  // neither +0 nor -0: negative, NaN or inf
+        }
+      }
+      if (validate) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = base + q * 32 + lane;
+          if (i < n && a.ids[plo + i] < 0) bad = true;
+        }
+      }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(&a.hdr->status, WS_EDATA);
 #pragma unroll
