@@ -187,28 +187,59 @@ def alu_roofline(st, kernel_ms):
     peak = props.multi_processor_count * LANES_PER_SM * mhz * 1e6 / 1e12
     work = st["kept"] * LANE_INST_PER_ARRIVAL + st["elements"] * LANE_INST_PER_SCREEN
     achieved = work / (kernel_ms * 1e-3) / 1e12
-    traffic = TRAFFIC["bytes"] if TRAFFIC["src_sha"] == kernel_source_sha() else None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-inst/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "fastgm_kernel<2, 0>", "kernel_ms": kernel_ms,
+            "kernel": "fastgm_kernel<2, 0>", "kernel_ms": kernel_ms,
             "peak_source": "derived: %d SMs x %d lanes x %.0f MHz" % (props.multi_processor_count, LANES_PER_SM, mhz),
             "work_lane_inst": work, "kept_arrivals": st["kept"], "screened_elements": st["elements"]}
 
 
-def fp64_pipe_view(kept, kernel_ms):
-    """The paper's arithmetic on the FP64 unit as a lower bound: every kept arrival
-    needs at least one FP64 -ln u and two FP64 products, so a design that computes
-    them there takes at least kept x (1 / log rate + 2 / product rate), the rates
-    measured here on the FP64 unit alone (include/gm_diag.h).  frac = that bound /
-    the main kernel's time (above 1: faster than any FP64-unit design could be)."""
+FP64_PEAK_TFLOPS = 1.25  # GB300's FP64 rate (the recipe's unit table); also measured live below
+
+
+def harmonic(n):
+    return float(np.sum(1.0 / np.arange(1, n + 1)))
+
+
+def fp64_roofline(n_rows_pos, k, kernel_ms, rates, kept, traffic):
+    """The main kernel against the roofline of the method's arithmetic on the FP64
+    unit, the bound the paper's per-arrival work sets: every row needs about k H_k
+    arrivals (those below y*, the O(k ln k) term of FastGM's cost), each one FP64
+    -ln u, two FP64 products and one FP64 sum.  A product or a sum takes one FP64
+    issue slot (one DFMA's); a logarithm the slots that one CUDA log(double) takes,
+    DFMA rate / log rate, both measured in this run.  achieved = algorithmic
+    slots x 2 FLOP / kernel time, in TFLOP/s; peak = GB300's FP64 rate, 1.25 TFLOP/s
+    (0.625 T DFMA/s; measured DFMA rate beside it).  The per-element screen is
+    HBM-bound (12 B per element) and far below this term, so t_min is this term.
+    The kernel computes -ln u on the integer pipes instead, so frac can exceed 1."""
+    log_slots = rates["dfma_per_s"] / rates["neg_log_per_s"]
+    arrivals = n_rows_pos * k * harmonic(k)
+    slots = arrivals * (log_slots + 3.0)
+    achieved = 2.0 * slots / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "alu", "pipe": "fp64 (the method's arithmetic)", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+            "kernel": "fastgm_kernel<2, 0>", "kernel_ms": kernel_ms,
+            "peak_source": "GB300 FP64 rate from the recipe's unit table; measured DFMA rate %.3g/s" %
+                           rates["dfma_per_s"],
+            "algorithmic_arrivals": arrivals, "fp64_slots_per_arrival": log_slots + 3.0,
+            "log_slots": log_slots, "kept_arrivals": kept, "t_min_ms": slots / rates["dfma_per_s"] * 1e3}
+
+
+def fp64_rates():
+    """DFMA, CUDA log(double) and DMUL rates of this GPU's FP64 unit (include/gm_diag.h)."""
     import ctypes
     import torch
     from paper_2302_05176_gb300 import gm
     L = gm.lib()
     vp = ctypes.c_void_p
+    L.gm_diag_fma.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp]
     L.gm_diag_neglog.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
     L.gm_diag_dmul.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
     st = vp(torch.cuda.current_stream().cuda_stream)
     P = lambda t: vp(t.data_ptr())
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, iters = nsm * 8, 2048
+    buf = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    dfma = 8.0 * iters * blocks * 256 / (_time_ms(lambda: L.gm_diag_fma(1, blocks, iters, P(buf), st)) * 1e-3)
     n = 1 << 23
     rng = np.random.default_rng(0)
     x = torch.from_numpy(rng.integers(0, 2**62, size=n, dtype=np.int64)).cuda()
@@ -216,9 +247,7 @@ def fp64_pipe_view(kept, kernel_ms):
     y = torch.empty(n, dtype=torch.float64, device="cuda")
     log_rate = n / (_time_ms(lambda: L.gm_diag_neglog(P(x), n, 1, P(y), st)) * 1e-3)
     mul_rate = n / (_time_ms(lambda: L.gm_diag_dmul(P(a), P(a), n, 1, P(y), st)) * 1e-3)
-    t_min = kept * (1.0 / log_rate + 2.0 / mul_rate) * 1e3
-    return {"bound": "fp64 unit (paper's arithmetic)", "t_min_ms": t_min, "kernel_ms": kernel_ms,
-            "frac": t_min / kernel_ms, "neg_log_per_s": log_rate, "mul_per_s": mul_rate, "kept_arrivals": kept}
+    return {"dfma_per_s": dfma, "neg_log_per_s": log_rate, "mul_per_s": mul_rate}
 
 
 def estimator_figures(s, y):
@@ -264,18 +293,16 @@ def estimator_figures(s, y):
 def _time_aux_cold(fn, reps=10):
     """Mean device time of the library kernels of fn(), from events the library
     records immediately before its first and after its last kernel
-    (gm_diag_time_aux_kernels), with L2 flushed (a 256 MB write) before each call."""
+    (gm_diag_time_aux_kernels), with L2 flushed (a 256 MB read) before each call."""
     import ctypes
     import torch
     from paper_2302_05176_gb300 import gm
     L = gm.lib()
     L.gm_diag_time_aux_kernels.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
-    if not _FLUSH:
-        _FLUSH.append(torch.empty(256 << 20, dtype=torch.uint8, device="cuda"))
     fn()
     total = 0.0
     for _ in range(reps):
-        _FLUSH[0].zero_()
+        _flush_l2()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         e1.record()
@@ -290,16 +317,25 @@ def _time_aux_cold(fn, reps=10):
 _FLUSH = []
 
 
-def _time_ms_cold(fn, reps=10):
-    """Mean device time of fn() with L2 flushed before each call (a 256 MB write
-    outside the timed events): for inputs smaller than the 129 MB L2."""
+def _flush_l2():
+    """Evict L2 by reading a 256 MB buffer (twice the 129 MB L2).  A read leaves
+    clean lines behind; a write would leave dirty ones, whose write-back the next
+    timed kernel would pay for."""
     import torch
     if not _FLUSH:
-        _FLUSH.append(torch.empty(256 << 20, dtype=torch.uint8, device="cuda"))
+        _FLUSH.append(torch.zeros(64 << 20, dtype=torch.float32, device="cuda"))
+        _FLUSH.append(torch.zeros(1, dtype=torch.float32, device="cuda"))
+    torch.sum(_FLUSH[0], dim=0, out=_FLUSH[1][0])
+
+
+def _time_ms_cold(fn, reps=10):
+    """Mean device time of fn() with L2 flushed before each call (a 256 MB read
+    outside the timed events): for inputs smaller than the 129 MB L2."""
+    import torch
     fn()
     total = 0.0
     for _ in range(reps):
-        _FLUSH[0].zero_()
+        _flush_l2()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         fn()
@@ -724,6 +760,9 @@ def main():
     d2h = n_rows * K_MAIN * (4 + 8)
 
     value = world * n_rows / (ms_main * 1e-3)
+    rates = fp64_rates()
+    n_pos_rows = int(np.count_nonzero(np.diff(X.row_ptr) > 0))
+    traffic_main = TRAFFIC["bytes"] if TRAFFIC["src_sha"] == kernel_source_sha() else None
     line = {
         "metric": METRIC, "value": value, "unit": "sketches/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_main, "higher_is_better": True, "scaling": "weak",
@@ -735,8 +774,9 @@ def main():
         "arrivals_per_sketch": st_main["arrivals"] / n_rows,
         "kept_arrivals_per_sketch": st_main["kept"] / n_rows,
         "k4096": {"sketches_per_s": world * n_rows / (ms_alt * 1e-3), "ms_per_step": ms_alt,
-                  "elements_per_s": world * nnz / (ms_alt * 1e-3),
-                  "roofline_frac": alu_roofline(st_alt, kms_alt)["frac"]},
+                  "elements_per_s": world * nnz / (ms_alt * 1e-3), "kernel_ms": kms_alt,
+                  "roofline_frac": fp64_roofline(n_pos_rows, K_ALT, kms_alt, rates, st_alt["kept"], None)["frac"],
+                  "alu_issue_frac": alu_roofline(st_alt, kms_alt)["frac"]},
         "plain_k1024": {"sketches_per_s": world * n_rows / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                         "elements_per_s": world * nnz / (ms_plain * 1e-3),
                         "arrivals_per_s": st_plain["arrivals"] / (ms_plain * 1e-3),
@@ -747,9 +787,9 @@ def main():
                         "arrivals_per_s": st_plain4["arrivals"] / (ms_plain4 * 1e-3),
                         "identical_to_fastgm": same_plain4},
         "speedup_vs_plain_k4096": ms_plain4 / ms_alt,
-        "roofline": alu_roofline(st_main, kms_main),
-        "hbm": hbm_figures(nnz, n_rows, K_MAIN, kms_main),
-        "fp64_view": fp64_pipe_view(st_main["kept"], kms_main),
+        "roofline": fp64_roofline(n_pos_rows, K_MAIN, kms_main, rates, st_main["kept"], traffic_main),
+        "roofline_views": {"alu_issue": alu_roofline(st_main, kms_main),
+                           "hbm": hbm_figures(nnz, n_rows, K_MAIN, kms_main)},
         "estimators": estimator_figures(s_main, y_main),
         "e2e": {"value": world * n_rows / e2e_s, "unit": "sketches/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -1060,27 +1100,65 @@ def _serve_once(args, reqs, bufs, burst=False):
 
 
 def learned_ablation(args, timed, sketch_call, dev_csr, s_main, y_main, ms_main, st_main, n_rows):
-    """Train the bound network on sketches of fresh synthetic rows (k in {256, 1024,
-    4096}), then time FastGM with its bound, with the closed-form bound (the main
-    step) and with no initial bound on the benchmark batch; check all three agree."""
+    """The learned first-pass bound: the network trained on 200,000 sketches of the
+    single-vector law (n+ = 1,000 of 10,000 dimensions, Uniform(0,1] weights, k in
+    {256, 1024, 4096}), then evaluated at k = 1024 on held-out rows of that law and
+    on the benchmark batch (the lognormal law it never saw): FastGM with its bound,
+    with the closed-form bound and without an initial bound (FastSearch's doubling
+    horizon); fallback rates, kept arrivals, time, bit-identity."""
     import torch
     from paper_2302_05176_gb300 import gm, learned
+    from paper_2302_05176_gb300 import workloads as W
     rp, ids, w = dev_csr
     t0 = time.perf_counter()
-    ts = learned.make_training_set(args.learned_rows, ks=(256, 1024, 4096), seed=1000)
+    ts = learned.make_training_set(args.learned_rows, ks=(256, 1024, 4096), seed=1000, law="single_vector")
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     params, hist = learned.train(ts, tau=LEARNED_TAU, steps=args.learned_steps)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     model = learned.BoundModel(params, margin=0.0, tau=LEARNED_TAU)
+    same = lambda a, b: bool(torch.equal(a[0], b[0]) and torch.equal(a[1].view(torch.int64), b[1].view(torch.int64)))
 
-    ms_l, kms_l, st_l, s_l, y_l = timed(
-        lambda s_out, y_out, ws: model.sketch(rp, ids, w, K_MAIN, SEED, s_out=s_out, y_out=y_out, ws=ws),
-        K_MAIN, args.steps, args.warmup, learned_ws=True)
-    ms_n, kms_n, st_n, s_n, y_n = timed(sketch_call(gm.gm_sketch, K_MAIN, gm.GM_BOUND_NONE), K_MAIN,
-                                        max(2, args.steps // 3), args.warmup)
-    same = lambda s, y: bool(torch.equal(s, s_main) and torch.equal(y.view(torch.int64), y_main.view(torch.int64)))
+    def evaluate(csr, steps):
+        crp, cids, cw = csr
+        nr = crp.numel() - 1
+        nz = cw.numel()
+
+        def run(call, learned_ws=False, st_=steps):
+            s_out = torch.empty((nr, K_MAIN), dtype=torch.int32, device="cuda")
+            y_out = torch.empty((nr, K_MAIN), dtype=torch.float64, device="cuda")
+            nbytes = gm.sketch_learned_workspace_bytes(nr, nz, K_MAIN) if learned_ws else \
+                gm.sketch_workspace_bytes(nr, nz, K_MAIN)
+            ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            for _ in range(3):
+                call(s_out, y_out, ws)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(st_):
+                call(s_out, y_out, ws)
+            e1.record()
+            torch.cuda.synchronize()
+            code, st = gm.gm_status(ws)
+            assert code == gm.GM_OK
+            return e0.elapsed_time(e1) / st_, st, (s_out, y_out)
+
+        ml, stl, ol = run(lambda s_, y_, ws: model.sketch(crp, cids, cw, K_MAIN, SEED, s_out=s_, y_out=y_, ws=ws),
+                          learned_ws=True)
+        mc, stc, oc = run(lambda s_, y_, ws: gm.gm_sketch(crp, cids, cw, K_MAIN, SEED, s_out=s_, y_out=y_, ws=ws))
+        mn, stn, on = run(lambda s_, y_, ws: gm.gm_sketch(crp, cids, cw, K_MAIN, SEED, flags=gm.GM_BOUND_NONE,
+                                                            s_out=s_, y_out=y_, ws=ws), st_=max(2, steps // 3))
+        return {"rows": nr, "nnz": nz,
+                "learned": {"ms": ml, "fallback_rate": stl["rows_fallback"] / nr, "kept_per_sketch": stl["kept"] / nr},
+                "closed_form": {"ms": mc, "fallback_rate": stc["rows_fallback"] / nr,
+                                "kept_per_sketch": stc["kept"] / nr},
+                "no_initial_bound": {"ms": mn, "kept_per_sketch": stn["kept"] / nr},
+                "speedup_vs_closed_form": mc / ml, "speedup_vs_no_initial_bound": mn / ml,
+                "identical": same(ol, oc) and same(on, oc)}
+
+    held_out = evaluate(W.single_vector_batch_device(777_777, n_rows=4096), args.steps)
+    bench_batch = evaluate((rp, ids, w), args.steps)
     # the pre-pass alone (features + network per row, gm_learned_bound): HBM-bound,
     # algorithmic bytes = the weights and row offsets read once, the bounds written once
     t_out = torch.empty(n_rows, dtype=torch.float32, device=rp.device)
@@ -1090,19 +1168,12 @@ def learned_ablation(args, timed, sketch_call, dev_csr, s_main, y_main, ms_main,
     pre_bytes = 8 * w.numel() + 8 * (n_rows + 1) + 4 * n_rows
     hbm_gbs, hbm_src = peaks()
     return {
-        "prepass": {"ms": pre_ms, "algorithmic_bytes": pre_bytes, "gbs": pre_bytes / (pre_ms * 1e-3) / 1e9,
-                    "hbm_frac": pre_bytes / (pre_ms * 1e-3) / 1e9 / hbm_gbs, "hbm_peak_source": hbm_src},
+        "train_law": "single_vector: n+ = 1000 of 10,000 dims, Uniform(0,1], k in {256, 1024, 4096}",
         "train_sketches": int(ts.target.numel()), "train_set_s": t1 - t0, "train_s": t2 - t1,
         "train_steps": args.learned_steps, "tau": LEARNED_TAU, "final_pinball_loss": hist[-1][1],
-        "sketches_per_s": n_rows / (ms_l * 1e-3), "ms_per_step": ms_l,
-        "fallback_rate": st_l["rows_fallback"] / n_rows,
-        "closed_form_fallback_rate": st_main["rows_fallback"] / n_rows,
-        "kept_arrivals_per_sketch": st_l["kept"] / n_rows,
-        "closed_form_kept_arrivals_per_sketch": st_main["kept"] / n_rows,
-        "no_bound": {"sketches_per_s": n_rows / (ms_n * 1e-3), "ms_per_step": ms_n,
-                     "kept_arrivals_per_sketch": st_n["kept"] / n_rows},
-        "speedup_vs_no_bound": ms_n / ms_l, "speedup_vs_closed_form": ms_main / ms_l,
-        "identical_to_closed_form": same(s_l, y_l), "no_bound_identical": same(s_n, y_n),
+        "held_out_single_vector_k1024": held_out, "lognormal_batch_k1024": bench_batch,
+        "prepass": {"ms": pre_ms, "algorithmic_bytes": pre_bytes, "gbs": pre_bytes / (pre_ms * 1e-3) / 1e9,
+                    "hbm_frac": pre_bytes / (pre_ms * 1e-3) / 1e9 / hbm_gbs, "hbm_peak_source": hbm_src},
     }
 
 

@@ -85,7 +85,9 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
           nbase = __shfl_sync(FULL, nbase, 0);
           if (nbase + lane < n) {
             nv = a.w[lo + nbase + lane];
+#if !GM_EXP_R1SCREEN
             nid = a.ids[lo + nbase + lane];
+#endif
           }
         }
         const int base = nbase;
@@ -119,6 +121,9 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
               else
                 a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | TAG_MEDIUM;
             } else {
+#if GM_EXP_R1SCREEN
+              if (!PF) idv = a.ids[lo + slot];
+#endif
               const Words wd = philox((uint32_t)idv, 0u, a.key0, a.key1);
               if (screen_out(wd.w1, vf, Tf, kf))
                 ++cnt.screened;  // first arrival certainly above T: nothing of it counts
@@ -448,7 +453,11 @@ void chunk_unit(const SketchArgs& a, int row, int chunk, int longi, int64_t lo, 
   Reg* g = a.long_regs + (int64_t)longi * k;
   if (chi > clo) {
     float tdummy;
+#if GM_EXP_NOLADDER
+    const bool ladder = false;
+#else
     const bool ladder = a.chunk_ladder && !row_bound(a, row, tdummy);
+#endif
     float sumc = 0.0f;
     int nposc = 1;
     long long t = read_clock();
@@ -656,31 +665,14 @@ static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
   return GM_OK;
 }
 
-// Elements per chunk of a long row: SPLIT_LEN, or (GM_CHUNK_UNITS_PER_CTA > 0)
-// about that many units per CTA of the persistent grid if the batch were all
-// long rows, whole pre-pass pieces, between 2 pieces and SPLIT_LEN.  (Measured:
-// 16,384-element chunks made the 16 x 10^6 Pareto launch slower, 0.478 against
-// 0.40 ms: each unit's phase barriers and merge cost more than the balance gained.)
-static int chunk_len_for(int64_t nnz, int grid) {
-  if (GM_CHUNK_UNITS_PER_CTA <= 0) return SPLIT_LEN;
-  int64_t c = nnz / ((int64_t)(grid > 0 ? grid : 1) * GM_CHUNK_UNITS_PER_CTA);
-  c = c / PIECE_LEN * PIECE_LEN;
-  if (c < 2 * PIECE_LEN) c = 2 * PIECE_LEN;
-  if (c > SPLIT_LEN) c = SPLIT_LEN;
-  return (int)c;
-}
-
 template <int ARITH>
 static int launch_all(SketchArgs a, bool plain, int nsm, cudaStream_t stream) {
   const size_t sm = plain ? plain_smem_bytes(a.k) : fast_smem_bytes(a.k, a.ndense);
   int grid = 0, rc;
-  {
-    int per_sm = 0;
-    const void* kern = plain ? (const void*)plain_kernel<ARITH> : (const void*)fastgm_kernel<ARITH, MODE_MAIN>;
-    if (allow_max_smem(kern) != GM_OK) return GM_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, sm) != cudaSuccess) return GM_ECUDA;
-    a.chunk_len = chunk_len_for(a.nnz, nsm * (per_sm > 0 ? per_sm : 1));
-  }
+  // Long rows are cut into SPLIT_LEN-element chunks.  (16,384-element chunks,
+  // for more units per CTA, made the 16 x 10^6 Pareto launch slower: 0.478 against
+  // 0.40 ms; each unit's phase barriers and merge cost more than the balance gained.)
+  a.chunk_len = SPLIT_LEN;
   const int max_units = a.n_rows + (int)((a.nnz + a.chunk_len - 1) / a.chunk_len) + a.max_long;
   plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);
   longprep_kernel<<<nsm * 8, PREP_THREADS, 0, stream>>>(a);

@@ -57,9 +57,14 @@ namespace gm {
 #ifndef GM_MED_SW
 #define GM_MED_SW 8
 #endif
-// Long-row chunk length policy (see chunk_len_for): 0 = SPLIT_LEN.
-#ifndef GM_CHUNK_UNITS_PER_CTA
-#define GM_CHUNK_UNITS_PER_CTA 0
+#ifndef GM_EXP_NOLADDER
+#define GM_EXP_NOLADDER 0
+#endif
+#ifndef GM_EXP_R1SCREEN
+#define GM_EXP_R1SCREEN 0
+#endif
+#ifndef GM_EXP_SIMPLEMERGE
+#define GM_EXP_SIMPLEMERGE 0
 #endif
 // Default routing by the expected number of arrivals below T (gm_tuning): light
 // lanes up to LIGHT_MAX, 8-lane segments up to MEDIUM_MAX, 32-lane warps up to

@@ -21,7 +21,7 @@ from dataclasses import dataclass, field
 import torch
 
 from . import gm
-from .workloads import lognormal_batch_device
+from .workloads import lognormal_batch_device, single_vector_batch_device
 
 
 @dataclass
@@ -31,15 +31,22 @@ class TrainingSet:
     ks: list = field(default_factory=list)
 
 
-def make_training_set(n_sketches=200_000, ks=(256, 1024, 4096), seed=1000, rows_per_batch=4096, device="cuda"):
-    """Sketch n_sketches synthetic rows (the lognormal_batch distribution, the k
-    values taken in turn per batch) with gm_sketch and keep (features, ln y*)."""
+LAWS = {"lognormal": lognormal_batch_device, "single_vector": single_vector_batch_device}
+
+
+def make_training_set(n_sketches=200_000, ks=(256, 1024, 4096), seed=1000, rows_per_batch=4096, device="cuda",
+                      law="lognormal"):
+    """Sketch n_sketches synthetic rows (law "lognormal": the lognormal_batch
+    distribution; "single_vector": rows of n+ = 1,000 of 10,000 dimensions with
+    Uniform(0,1] weights; the k values taken in turn per batch) with gm_sketch and
+    keep (features, ln y*)."""
+    draw = LAWS[law]
     feats, target, klist = [], [], []
     done, b = 0, 0
     while done < n_sketches:
         n = min(rows_per_batch, n_sketches - done)
         k = int(ks[b % len(ks)])
-        row_ptr, ids, w = lognormal_batch_device(seed + b, n_rows=n, device=device)
+        row_ptr, ids, w = draw(seed + b, n_rows=n, device=device)
         _, y, ws = gm.gm_sketch(row_ptr, ids, w, k, seed + 7919 * b)
         t = gm.gm_row_ln_ystar(y)
         f = gm.gm_features(row_ptr, ids, w, k)

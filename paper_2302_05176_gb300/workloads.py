@@ -129,6 +129,29 @@ def lognormal_batch_device(seed, n_rows=4096, median=2000.0, sigma=1.0, lo=10, h
     return row_ptr, ids, w
 
 
+def single_vector_batch_device(seed, n_rows=4096, n_dims=10_000, n_pos=1_000, device="cuda"):
+    """Rows of the single_vector law drawn on the device: n_pos positive entries of
+    n_dims dimensions, weights Uniform(0, 1].  The ids of row r are the progression
+    (a_r + i s_r) mod n_dims with a random start and a random step coprime to
+    n_dims (so distinct within the row); the sketch keys its random numbers on the
+    id, so this structure is immaterial.  Returns device tensors (row_ptr int64,
+    ids int32, w float64)."""
+    import math
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    units = torch.tensor([s for s in range(1, n_dims) if math.gcd(s, n_dims) == 1], dtype=torch.int64,
+                         device=device)
+    row_ptr = torch.arange(n_rows + 1, dtype=torch.int64, device=device) * n_pos
+    start = torch.randint(0, n_dims, (n_rows, 1), generator=g, device=device, dtype=torch.int64)
+    step = units[torch.randint(0, units.numel(), (n_rows, 1), generator=g, device=device)]
+    pos = torch.arange(n_pos, dtype=torch.int64, device=device)[None, :]
+    ids = ((start + pos * step) % n_dims).reshape(-1).to(torch.int32)
+    w = 1.0 - torch.rand(n_rows * n_pos, generator=g, device=device, dtype=torch.float64)
+    return row_ptr, ids, w
+
+
 def pareto_weights(rng, n, alpha, x_min):
     return x_min * (1.0 + rng.pareto(alpha, size=n))
 
