@@ -367,6 +367,28 @@ int gm_sketch_bounded(const int64_t* row_ptr, const int32_t* ids, const double* 
                       double* y_out, void* workspace, size_t workspace_bytes, void* stream);
 int gm_row_ystar(const double* y, int32_t n_rows, int32_t k, double* out, void* stream);
 
+/*
+ * gm_sketch_fastsearch -- FastGM under the paper's own FastSearch schedule
+ * (Algorithm 1, Sec. 2.2), all on the device: each row is taken by one CTA,
+ * which runs the rounds R = delta, 2 delta, ... -- element i releases the first
+ * min(k, ceil(R (v_i / sum v))) arrivals of its stream (sum v in FP64 in a fixed
+ * order; the ratio and the product in FP64, then the ceiling) -- until every
+ * register holds an arrival, then FastPrune: every element streams until its
+ * arrival exceeds the row's y* = max_j y_j.  An element whose budget did not grow
+ * in a round releases nothing in it; one whose budget grew releases its stream
+ * again from the first arrival (register updates are idempotent).  After 4,096
+ * rounds a last round releases every arrival.  Same registers as gm_sketch.
+ *   delta       >= 1 (Algorithm 1 takes delta = k)
+ *   rounds_out  device int32[n_rows] (nullable): the rounds each row took, so the
+ *               budget at which FastSearch found every register filled is
+ *               rounds_out[r] * delta (0 for a row without positive weights)
+ * flags: GM_FLAG_VALIDATE and the arithmetic flags.  Workspace: as gm_sketch.
+ * gm_status's rows_escalated counts the rounds beyond the first, summed over rows.
+ */
+int gm_sketch_fastsearch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
+                         int32_t k, uint64_t seed, uint32_t flags, int32_t delta, int32_t* rounds_out,
+                         int32_t* s_out, double* y_out, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---- Stream-FastGM (Algorithm 2, Sec. 3 of the paper: the extension to streams) --
  * A stream of elements, each occurring any number of times with a fixed weight,
  * folded chunk by chunk into one running sketch (s int32[k], y double[k] on the

@@ -66,6 +66,44 @@ __device__ __forceinline__ void acc_term(Acc128& a, unsigned long long b, int em
   }
 }
 
+// The accumulator's value, acc 2^(emax - 1135), rounded to the nearest double
+// (ties to even).  acc > 0.
+__device__ __forceinline__ double acc_to_double(const Acc128& acc, int emax) {
+  // round (hi:lo) to 53 bits, ties to even; value = (hi:lo) 2^(emax - 1135)
+  const int lz = acc.hi ? __clzll((long long)acc.hi) : 64 + __clzll((long long)acc.lo);
+  const int drop = (127 - lz) - 52;  // bits below the 53-bit significand (the sum is >= 2^60 here)
+  unsigned long long mant, rh, rl;    // rh:rl: the dropped bits, left-aligned
+  if (drop <= 0) {
+    mant = acc.lo << (-drop);
+    rh = rl = 0ull;
+  } else if (drop < 64) {
+    mant = (acc.lo >> drop) | (acc.hi << (64 - drop));
+    rh = acc.lo << (64 - drop);
+    rl = 0ull;
+  } else if (drop == 64) {
+    mant = acc.hi;
+    rh = acc.lo;
+    rl = 0ull;
+  } else {
+    mant = acc.hi >> (drop - 64);
+    rh = (acc.hi << (128 - drop)) | (acc.lo >> (drop - 64));
+    rl = acc.lo << (128 - drop);
+  }
+  const bool rb = (rh >> 63) != 0ull;
+  const bool sticky = ((rh << 1) | rl) != 0ull;
+  mant += (rb && (sticky || (mant & 1ull))) ? 1ull : 0ull;
+  int e2 = emax - 1135 + drop;  // exponent of the significand's lowest bit
+  if (mant >> 53) {             // rounding carried into a new binade
+    mant >>= 1;
+    ++e2;
+  }
+  const int eb = e2 + 1075;  // biased exponent of the result
+  const double sum = (eb >= 1 && eb <= 2046)
+                         ? __longlong_as_double((long long)(((unsigned long long)eb << 52) | (mant & 0x000FFFFFFFFFFFFFull)))
+                         : ldexp((double)mant, e2);
+  return sum;
+}
+
 // (k - 1) / sum_j y_j by one warp; every lane returns it.  The sum is formed on
 // the integer pipes, not the FP64 unit (whose add rate, not HBM, would bound the
 // estimator on GB300): each lane adds its registers into a 128-bit fixed-point
@@ -126,39 +164,113 @@ __device__ __forceinline__ double warp_cardinality(const double* __restrict__ y,
     const unsigned long long hi = __shfl_xor_sync(0xFFFFFFFFu, acc.hi, d);
     acc_add(acc, lo, hi);
   }
-  // round (hi:lo) to 53 bits, ties to even; value = (hi:lo) 2^(emax - 1135)
-  const int lz = acc.hi ? __clzll((long long)acc.hi) : 64 + __clzll((long long)acc.lo);
-  const int drop = (127 - lz) - 52;  // bits below the 53-bit significand (the sum is >= 2^60 here)
-  unsigned long long mant, rh, rl;    // rh:rl: the dropped bits, left-aligned
-  if (drop <= 0) {
-    mant = acc.lo << (-drop);
-    rh = rl = 0ull;
-  } else if (drop < 64) {
-    mant = (acc.lo >> drop) | (acc.hi << (64 - drop));
-    rh = acc.lo << (64 - drop);
-    rl = 0ull;
-  } else if (drop == 64) {
-    mant = acc.hi;
-    rh = acc.lo;
-    rl = 0ull;
+  return (double)(k - 1) / acc_to_double(acc, emax);
+}
+
+
+// The same estimates by one CTA of NT threads per row or pair (the batch kernels):
+// thread t takes registers t, t + NT, ... (16-byte loads when aligned), so a row
+// is read in one round trip; partial results meet in shared memory.  The integer
+// hit count and the exactly aligned sum do not depend on the partition, so these
+// give the same bits as the warp versions above.
+template <int NT>
+__device__ __forceinline__ double block_jaccard(const int32_t* __restrict__ a, const int32_t* __restrict__ b, int k,
+                                                int* red) {
+  const int tid = threadIdx.x;
+  int hits = 0;
+  if ((k & 3) == 0 && ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0) {
+    const int4* a4 = reinterpret_cast<const int4*>(a);
+    const int4* b4 = reinterpret_cast<const int4*>(b);
+#pragma unroll 4
+    for (int j = tid; j < (k >> 2); j += NT) {
+      const int4 x = __ldg(a4 + j), y = __ldg(b4 + j);
+      hits += (x.x >= 0 && x.x == y.x) + (x.y >= 0 && x.y == y.y) + (x.z >= 0 && x.z == y.z) +
+              (x.w >= 0 && x.w == y.w);
+    }
   } else {
-    mant = acc.hi >> (drop - 64);
-    rh = (acc.hi << (128 - drop)) | (acc.lo >> (drop - 64));
-    rl = acc.lo << (128 - drop);
+#pragma unroll 4
+    for (int j = tid; j < k; j += NT) {
+      const int32_t x = __ldg(a + j), y = __ldg(b + j);
+      hits += (x >= 0 && x == y) ? 1 : 0;
+    }
   }
-  const bool rb = (rh >> 63) != 0ull;
-  const bool sticky = ((rh << 1) | rl) != 0ull;
-  mant += (rb && (sticky || (mant & 1ull))) ? 1ull : 0ull;
-  int e2 = emax - 1135 + drop;  // exponent of the significand's lowest bit
-  if (mant >> 53) {             // rounding carried into a new binade
-    mant >>= 1;
-    ++e2;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) hits += __shfl_xor_sync(0xFFFFFFFFu, hits, d);
+  if ((tid & 31) == 0) red[tid >> 5] = hits;
+  __syncthreads();
+  int total = 0;
+#pragma unroll
+  for (int q = 0; q < NT / 32; ++q) total += red[q];
+  __syncthreads();
+  return (double)total / (double)k;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_cardinality(const double* __restrict__ y, int k, unsigned long long* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool vec = (k & 1) == 0 && (reinterpret_cast<uintptr_t>(y) & 15u) == 0;
+  const double2* y2 = reinterpret_cast<const double2*>(y);
+  // pass 1: the largest bit pattern (bits compare like the values)
+  unsigned long long bmax = 0ull;
+  if (vec) {
+#pragma unroll 4
+    for (int j = tid; j < (k >> 1); j += NT) {
+      const double2 v = __ldg(y2 + j);
+      const unsigned long long p = (unsigned long long)__double_as_longlong(v.x);
+      const unsigned long long q = (unsigned long long)__double_as_longlong(v.y);
+      bmax = p > bmax ? p : bmax;
+      bmax = q > bmax ? q : bmax;
+    }
+  } else {
+#pragma unroll 4
+    for (int j = tid; j < k; j += NT) {
+      const unsigned long long p = (unsigned long long)__double_as_longlong(__ldg(y + j));
+      bmax = p > bmax ? p : bmax;
+    }
   }
-  const int eb = e2 + 1075;  // biased exponent of the result
-  const double sum = (eb >= 1 && eb <= 2046)
-                         ? __longlong_as_double((long long)(((unsigned long long)eb << 52) | (mant & 0x000FFFFFFFFFFFFFull)))
-                         : ldexp((double)mant, e2);
-  return (double)(k - 1) / sum;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, bmax, d);
+    bmax = o > bmax ? o : bmax;
+  }
+  if (lane == 0) red[warp] = bmax;
+  __syncthreads();
+  bmax = 0ull;
+#pragma unroll
+  for (int q = 0; q < NT / 32; ++q) bmax = red[q] > bmax ? red[q] : bmax;
+  __syncthreads();
+  if (bmax >= 0x7FF0000000000000ull) return 0.0;  // an unfilled register (or a NaN)
+  if (bmax == 0ull) return (double)(k - 1) / 0.0;
+  const int emax = (int)(bmax >> 52) ? (int)(bmax >> 52) : 1;
+  // pass 2: the aligned sum (the thread's own registers, from L1)
+  Acc128 acc{0ull, 0ull};
+  if (vec) {
+#pragma unroll 4
+    for (int j = tid; j < (k >> 1); j += NT) {
+      const double2 v = __ldg(y2 + j);
+      acc_term(acc, (unsigned long long)__double_as_longlong(v.x), emax);
+      acc_term(acc, (unsigned long long)__double_as_longlong(v.y), emax);
+    }
+  } else {
+#pragma unroll 4
+    for (int j = tid; j < k; j += NT) acc_term(acc, (unsigned long long)__double_as_longlong(__ldg(y + j)), emax);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned long long lo = __shfl_xor_sync(0xFFFFFFFFu, acc.lo, d);
+    const unsigned long long hi = __shfl_xor_sync(0xFFFFFFFFu, acc.hi, d);
+    acc_add(acc, lo, hi);
+  }
+  if (lane == 0) {
+    red[2 * warp] = acc.lo;
+    red[2 * warp + 1] = acc.hi;
+  }
+  __syncthreads();
+  Acc128 tot{0ull, 0ull};
+#pragma unroll
+  for (int q = 0; q < NT / 32; ++q) acc_add(tot, red[2 * q], red[2 * q + 1]);
+  __syncthreads();
+  return (double)(k - 1) / acc_to_double(tot, emax);
 }
 
 }  // namespace gm

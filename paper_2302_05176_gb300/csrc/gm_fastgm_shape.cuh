@@ -80,25 +80,23 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
     uint32_t nmask = __ballot_sync(FULL, e < 0);
     while (nmask && !(pool_done && wcount == 0)) {
       if (wcount == 0) {
-        if (!PF) {
-          if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
-          nbase = __shfl_sync(FULL, nbase, 0);
-          if (nbase + lane < n) {
-            nv = a.w[lo + nbase + lane];
-#if !GM_EXP_R1SCREEN
-            nid = a.ids[lo + nbase + lane];
-#endif
-          }
+        int base = 0;
+        double v = 0.0;
+        int32_t idv = 0;
+        if (PF) {
+          base = nbase;
+          v = nv;
+          idv = nid;
+        } else {
+          if (lane == 0) base = atomicAdd(&sh.pool, 32);
+          base = __shfl_sync(FULL, base, 0);
         }
-        const int base = nbase;
         if (base >= n) {
           pool_done = true;
           break;
         }
         const int slot = base + lane;
         bool surv = false;
-        double v = nv;
-        int32_t idv = nid;
         if (PF) {
           if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
           nbase = __shfl_sync(FULL, nbase, 0);
@@ -108,6 +106,7 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
           }
         }
         if (slot < n) {
+          if (!PF) v = a.w[lo + slot];
           if (positive_finite(v)) {
             ++cnt.elements;
             const float vf = f32_trunc(v);
@@ -121,9 +120,7 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
               else
                 a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | TAG_MEDIUM;
             } else {
-#if GM_EXP_R1SCREEN
               if (!PF) idv = a.ids[lo + slot];
-#endif
               const Words wd = philox((uint32_t)idv, 0u, a.key0, a.key1);
               if (screen_out(wd.w1, vf, Tf, kf))
                 ++cnt.screened;  // first arrival certainly above T: nothing of it counts
@@ -214,6 +211,145 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
   }
 }
 
+// FastSearch's release step (Algorithm 1) on the light path: every positive
+// element of [lo, lo+n) whose budget grew from bRprev to bR releases the first
+// fs_budget(bR) arrivals of its stream (one lane each, from its first arrival:
+// register updates are idempotent minima, so re-releasing the earlier ones
+// changes nothing); larger budgets go to the work list for the segment phases.
+// Elements whose budget did not grow have nothing new to release.
+template <int ARITH>
+__device__ __forceinline__ void budget_light_phase(const SketchArgs& a, int64_t lo, int n, double bR, double bRprev,
+                                                   double bsum, Reg* regs, uint32_t* map, unsigned char* wbuf,
+                                                   SmemScalars& sh, Counters& cnt, bool& gave_up) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  double* wb_r = reinterpret_cast<double*>(wbuf);
+  uint32_t* wb_slot = reinterpret_cast<uint32_t*>(wbuf + 256);
+  int32_t* wb_id = reinterpret_cast<int32_t*>(wbuf + 384);
+  const int k = a.k;
+  int e = -1, z = 0, msize = 0, lim = 0;
+  int32_t id = 0;
+  double R = 0.0;
+  Fix acc = fix_zero();
+  int wcount = 0;
+  bool pool_done = false;
+  while (true) {
+    uint32_t nmask = __ballot_sync(FULL, e < 0);
+    while (nmask && !(pool_done && wcount == 0)) {
+      if (wcount == 0) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&sh.pool, 32);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= n) {
+          pool_done = true;
+          break;
+        }
+        const int slot = base + lane;
+        bool surv = false;
+        double v = 0.0;
+        int32_t idv = 0;
+        if (slot < n) {
+          v = a.w[lo + slot];
+          if (positive_finite(v)) {
+            ++cnt.elements;
+            const int b = fs_budget(bR, v, bsum, k), bp = fs_budget(bRprev, v, bsum, k);
+            if (b == bp) {
+              ++cnt.screened;  // nothing new: its released arrivals are in the registers
+            } else if ((float)b > a.light_max) {
+              if ((float)b > a.medium_max)
+                a.list[lo + n - 1 - atomicAdd(&sh.bcount, 1)] =
+                    (uint32_t)slot | ((float)b > a.heavy_max ? TAG_SUPER : TAG_HEAVY);
+              else
+                a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | TAG_MEDIUM;
+            } else {
+              idv = a.ids[lo + slot];
+              surv = true;
+            }
+          }
+        }
+        const uint32_t sm = __ballot_sync(FULL, surv);
+        if (surv) {
+          const int p = __popc(sm & lanemask_lt());
+          wb_r[p] = arr_rcp<ARITH>(v);
+          wb_slot[p] = (uint32_t)slot;
+          wb_id[p] = idv;
+        }
+        wcount = __popc(sm);
+        __syncwarp();
+        continue;
+      }
+      const int take = min(__popc(nmask), wcount);
+      const int rank = __popc(nmask & lanemask_lt());
+      if (e < 0 && rank < take) {
+        const int q = wcount - 1 - rank;
+        e = (int)wb_slot[q];
+        id = wb_id[q];
+        R = wb_r[q];
+        z = 0;
+        acc = fix_zero();
+        msize = 0;
+        lim = fs_budget(bR, a.w[lo + e], bsum, k);
+      }
+      wcount -= take;
+      __syncwarp();
+      nmask = __ballot_sync(FULL, e < 0);
+    }
+    if (!__any_sync(FULL, e >= 0)) break;
+    if (e < 0) continue;
+    if (z >= lim) {  // its release is spent
+      e = -1;
+      continue;
+    }
+    int J;
+    fix_add(acc, arrival_term<ARITH>(id, z, k, a.key0, a.key1, a.ctab, J));
+    const uint64_t bb = (uint64_t)__double_as_longlong(arr_mul<ARITH>(fix_round(acc), R));
+    ++cnt.arrivals;
+    int iz = -1;
+    for (int i = 0; i < msize; ++i)
+      if ((map[i * BLOCK + tid] >> 16) == (uint32_t)z) {
+        iz = i;
+        break;
+      }
+    uint32_t vz = (uint32_t)z;
+    if (iz >= 0) {
+      vz = map[iz * BLOCK + tid] & 0xFFFFu;
+      --msize;
+      map[iz * BLOCK + tid] = map[msize * BLOCK + tid];
+    }
+    uint32_t c = vz;
+    bool overflow = false;
+    if (J != z) {
+      int ij = -1;
+      for (int i = 0; i < msize; ++i)
+        if ((map[i * BLOCK + tid] >> 16) == (uint32_t)J) {
+          ij = i;
+          break;
+        }
+      if (ij >= 0) {
+        c = map[ij * BLOCK + tid] & 0xFFFFu;
+        map[ij * BLOCK + tid] = ((uint32_t)J << 16) | vz;
+      } else {
+        c = (uint32_t)J;
+        if (msize >= MAPCAP) {
+          overflow = true;
+        } else {
+          map[msize * BLOCK + tid] = ((uint32_t)J << 16) | vz;
+          ++msize;
+        }
+      }
+    }
+    if (overflow) {  // restart this element on an 8-lane segment
+      a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)e | TAG_MEDIUM;
+      e = -1;
+      continue;
+    }
+    if (bb <= DBL_MAX_BITS) {  // an arrival that is not finite takes no register
+      cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
+      ++cnt.kept;
+    }
+    if (++z >= k) e = -1;
+  }
+}
+
 __device__ __forceinline__ void clk_add(Counters&, int which, long long& t) {
   const long long now = read_clock();
   if ((threadIdx.x & 31) == 0) sh_scalars.clk[threadIdx.x >> 5][which] += (unsigned long long)(now - t);
@@ -225,33 +361,34 @@ __device__ __forceinline__ void clk_add(Counters&, int which, long long& t) {
 // in both), then the elements promoted out of 8-lane segments, then dense
 // permutations (warps < ndense).  (Lowering T to the running y* at the barriers
 // saved 2 % of the arrivals and cost more in barriers: measured and dropped.)
-template <int ARITH>
+// BUDGET: FastSearch's release of budget bR (row sum bsum) instead of the bound.
+template <int ARITH, bool BUDGET = false>
 __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, int n, uint64_t Tbits, Reg* regs,
                                             uint32_t* area, uint16_t* dense, SmemScalars& sh, Counters& cnt,
-                                            bool& gave_up, long long& t) {
+                                            bool& gave_up, long long& t, double bR = 0.0, double bsum = 0.0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nh = sh.hcount, nb = sh.bcount;
   uint32_t* back = a.list + lo + n - nb;  // the 32-lane and dense entries
   {
     const int seg = lane / MED_SW;
     const HashPiN<MED_SLOTS> hp{area + (warp * (32 / MED_SW) + seg) * MED_SLOTS};
-    seg_phase<ARITH, MED_SW>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_med, TAG_MEDIUM, hp, MED_MAX_FILL,
-                             a.plist + lo, &sh.pcount, cnt, gave_up);
+    seg_phase<ARITH, MED_SW, HashPiN<MED_SLOTS>, BUDGET>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_med, TAG_MEDIUM, hp, MED_MAX_FILL,
+                             a.plist + lo, &sh.pcount, cnt, gave_up, bR, bsum);
   }
   clk_add(cnt, CLK_MEDIUM, t);
   // a warp's hash region is the same in both phases: the heavy list needs no barrier
   {
     const HashPi hp{area + warp * HASH_SLOTS};
-    seg_phase<ARITH, 32>(a, lo, Tbits, regs, back, nb, &sh.c_heavy, TAG_HEAVY, hp, HASH_MAX_FILL, nullptr, nullptr,
-                         cnt, gave_up);
+    seg_phase<ARITH, 32, HashPi, BUDGET>(a, lo, Tbits, regs, back, nb, &sh.c_heavy, TAG_HEAVY, hp, HASH_MAX_FILL, nullptr, nullptr,
+                         cnt, gave_up, bR, bsum);
   }
   clk_add(cnt, CLK_HEAVY, t);
   __syncthreads();  // every promotion is listed
   clk_add(cnt, CLK_WAIT, t);
   {
     const HashPi hp{area + warp * HASH_SLOTS};
-    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_pheavy, TAG_HEAVY, hp, HASH_MAX_FILL,
-                         nullptr, nullptr, cnt, gave_up);
+    seg_phase<ARITH, 32, HashPi, BUDGET>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_pheavy, TAG_HEAVY, hp, HASH_MAX_FILL,
+                         nullptr, nullptr, cnt, gave_up, bR, bsum);
   }
   clk_add(cnt, CLK_HEAVY, t);
   __syncthreads();
@@ -262,10 +399,10 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, int
     uint16_t* mine = warp < a.ndense ? dense + (size_t)warp * pi_stride(a.k)
                                      : reinterpret_cast<uint16_t*>(area) + (size_t)(warp - a.ndense) * pi_stride(a.k);
     const DensePi dp{mine};
-    seg_phase<ARITH, 32>(a, lo, Tbits, regs, back, nb, &sh.c_super, TAG_SUPER, dp, 1 << 30, nullptr, nullptr, cnt,
-                         gave_up);
-    seg_phase<ARITH, 32>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_psuper, TAG_SUPER, dp, 1 << 30,
-                         nullptr, nullptr, cnt, gave_up);
+    seg_phase<ARITH, 32, DensePi, BUDGET>(a, lo, Tbits, regs, back, nb, &sh.c_super, TAG_SUPER, dp, 1 << 30, nullptr, nullptr, cnt,
+                         gave_up, bR, bsum);
+    seg_phase<ARITH, 32, DensePi, BUDGET>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_psuper, TAG_SUPER, dp, 1 << 30,
+                         nullptr, nullptr, cnt, gave_up, bR, bsum);
   }
   clk_add(cnt, CLK_SUPER, t);
   __syncthreads();
@@ -439,6 +576,69 @@ __device__ __forceinline__ bool ladder_bound(const Reg* g, int k, float sumc, in
   return final;
 }
 
+// One row by one CTA under the paper's FastSearch schedule (Algorithm 1): rounds
+// R = Delta, 2 Delta, ... release each element's first ceil(R v / sum v) arrivals
+// (sum v in FP64, a fixed order) until every register holds an arrival; then
+// FastPrune: every element streams up to the row's y* = max_j y_j (arrivals equal
+// to y* still take part in the tie rule).  After FS_MAX_ROUNDS rounds a last one
+// releases every arrival.  Writes the row and the number of rounds it took.
+template <int ARITH>
+__device__ __forceinline__ void fastsearch_row(const SketchArgs& a, int row, int64_t lo, int n, Reg* regs,
+                                               uint32_t* area, uint16_t* dense, unsigned char* wbuf,
+                                               SmemScalars& sh, Counters& cnt, bool& gave_up) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float sumv;
+  int npos;
+  long long t = read_clock();
+  block_sum<BLOCK>(a, lo, n, sh.red_f, sh.red_i, sumv, npos);
+  const double dsum = block_dsum<BLOCK>(a.w, lo, n, sh.red_d);
+  int rounds = 0;
+  if (npos > 0) {
+    for (int r = 1;; ++r) {
+      const bool all = r > FS_MAX_ROUNDS;
+      const double bR = all ? __longlong_as_double((long long)INF_BITS) : (double)r * (double)a.fs_delta;
+      const double bRprev = (double)(r - 1) * (double)a.fs_delta;
+      reset_lists(sh);
+      __syncthreads();
+      budget_light_phase<ARITH>(a, lo, n, bR, bRprev, dsum, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt,
+                                gave_up);
+      __syncthreads();
+      warp_phases<ARITH, true>(a, lo, n, DBL_MAX_BITS, regs, area, dense, sh, cnt, gave_up, t, bR, dsum);
+      rounds = r;
+      int empty = 0;
+      for (int j = tid; j < a.k; j += BLOCK) empty |= (regs[j].y == INF_BITS);
+      if (!__syncthreads_or(empty) || all) break;
+    }
+    // FastPrune by the row's y*
+    unsigned long long m = 0ull;
+    for (int j = tid; j < a.k; j += BLOCK) m = regs[j].y > m ? regs[j].y : m;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(FULL, m, d);
+      m = o > m ? o : m;
+    }
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(sh.red_d);
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    m = 0ull;
+    for (int q = 0; q < WARPS; ++q) m = red[q] > m ? red[q] : m;
+    __syncthreads();
+    if (m < INF_BITS) {
+      const float Tf = fmaxf(__double2float_ru(__longlong_as_double((long long)m)), 1.17549435e-38f);
+      reset_lists(sh);
+      __syncthreads();
+      light_phase<ARITH, false>(a, lo, n, m, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt, gave_up);
+      __syncthreads();
+      warp_phases<ARITH>(a, lo, n, m, regs, area, dense, sh, cnt, gave_up, t);
+    }
+  }
+  write_out(a, row, regs);
+  if (tid == 0) {
+    if (a.fs_rounds) a.fs_rounds[row] = rounds;
+    if (rounds > 1) cnt.escalated += (uint32_t)(rounds - 1);
+  }
+}
+
 // One chunk of a long row: its elements with the bound from the row's sum (or,
 // in the bound-free mode, a ladder of passes on the chunk's own registers), then
 // its registers merged into the row's global ones.
@@ -453,11 +653,7 @@ void chunk_unit(const SketchArgs& a, int row, int chunk, int longi, int64_t lo, 
   Reg* g = a.long_regs + (int64_t)longi * k;
   if (chi > clo) {
     float tdummy;
-#if GM_EXP_NOLADDER
-    const bool ladder = false;
-#else
     const bool ladder = a.chunk_ladder && !row_bound(a, row, tdummy);
-#endif
     float sumc = 0.0f;
     int nposc = 1;
     long long t = read_clock();
@@ -507,10 +703,12 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
   if ((tid & 31) == 0)
     for (int q = 0; q < NCLK; ++q) sh.clk[tid >> 5][q] = 0ull;
   const uint32_t n_extra = a.hdr->n_extra, n_long = a.hdr->n_long;
-  const uint32_t n_units = MODE == MODE_MAIN ? n_extra + (uint32_t)a.n_rows : a.hdr->esc_count;
+  const uint32_t n_units = MODE == MODE_MAIN ? n_extra + (uint32_t)a.n_rows
+                           : MODE == MODE_FS ? (uint32_t)a.n_rows
+                                             : a.hdr->esc_count;
 
   while (true) {
-    if (tid == 0) sh.unit = (int)atomicAdd(MODE == MODE_MAIN ? &a.hdr->unit_counter : &a.hdr->esc_counter, 1u);
+    if (tid == 0) sh.unit = (int)atomicAdd(MODE == MODE_ESC ? &a.hdr->esc_counter : &a.hdr->unit_counter, 1u);
     __syncthreads();
     const uint32_t u = (uint32_t)sh.unit;
     if (u >= n_units) break;
@@ -519,12 +717,21 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
       row = (int)a.esc[u];
       chunk = 0;
       longi = -1;
+    } else if (MODE == MODE_FS) {
+      row = (int)u;
+      chunk = 0;
+      longi = -1;
     } else {
       resolve_unit(a, u, n_extra, n_long, row, chunk, longi);
     }
     int64_t lo, hi;
     row_bounds(a, row, lo, hi);
     init_regs(a, regs, k);
+    if constexpr (MODE == MODE_FS) {
+      fastsearch_row<ARITH>(a, row, lo, (int)(hi - lo), regs, area, dense, wbuf, sh, cnt, gave_up);
+      __syncthreads();
+      continue;
+    }
     if (longi < 0) {  // the whole row in this CTA
       fastgm_row<ARITH>(a, row, lo, (int)(hi - lo), MODE == MODE_ESC ? 1 : 0, regs, area, dense, wbuf, sh, cnt,
                         gave_up);
@@ -674,8 +881,10 @@ static int launch_all(SketchArgs a, bool plain, int nsm, cudaStream_t stream) {
   // 0.40 ms; each unit's phase barriers and merge cost more than the balance gained.)
   a.chunk_len = SPLIT_LEN;
   const int max_units = a.n_rows + (int)((a.nnz + a.chunk_len - 1) / a.chunk_len) + a.max_long;
-  plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);
-  longprep_kernel<<<nsm * 8, PREP_THREADS, 0, stream>>>(a);
+  if (a.fs_delta == 0) {  // FastSearch's schedule takes every row whole: no long-row plan
+    plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);
+    longprep_kernel<<<nsm * 8, PREP_THREADS, 0, stream>>>(a);
+  }
   if (plain) {
     if constexpr (BLOCK != 512) {
       return GM_EINVAL;  // the plain sketch runs with 512-thread CTAs only
@@ -687,6 +896,14 @@ static int launch_all(SketchArgs a, bool plain, int nsm, cudaStream_t stream) {
       if (g_main_after) cudaEventRecord(g_main_after, stream);
       return GM_OK;
     }
+  }
+  if (a.fs_delta > 0) {  // FastSearch's schedule: every row whole, no chunks, no redo kernel
+    rc = occupancy_grid(fastgm_kernel<ARITH, MODE_FS>, sm, nsm, a.n_rows, grid);
+    if (rc != GM_OK) return rc;
+    if (g_main_before) cudaEventRecord(g_main_before, stream);
+    fastgm_kernel<ARITH, MODE_FS><<<grid, BLOCK, sm, stream>>>(a);
+    if (g_main_after) cudaEventRecord(g_main_after, stream);
+    return GM_OK;
   }
   rc = occupancy_grid(fastgm_kernel<ARITH, MODE_MAIN>, sm, nsm, max_units, grid);
   if (rc != GM_OK) return rc;

@@ -57,15 +57,6 @@ namespace gm {
 #ifndef GM_MED_SW
 #define GM_MED_SW 8
 #endif
-#ifndef GM_EXP_NOLADDER
-#define GM_EXP_NOLADDER 0
-#endif
-#ifndef GM_EXP_R1SCREEN
-#define GM_EXP_R1SCREEN 0
-#endif
-#ifndef GM_EXP_SIMPLEMERGE
-#define GM_EXP_SIMPLEMERGE 0
-#endif
 // Default routing by the expected number of arrivals below T (gm_tuning): light
 // lanes up to LIGHT_MAX, 8-lane segments up to MEDIUM_MAX, 32-lane warps up to
 // HEAVY_MAX, dense permutations beyond; first-pass bound at quantile 1 - P_FIRST.
@@ -121,7 +112,18 @@ struct SketchArgs {
   const int32_t* init_s;  // stream mode (one row): registers start from this sketch, else unfilled
   const double* init_y;
   const double* r_row;    // budget pass (plain kernel): FastSearch's R per row, else null
+  int fs_delta;           // FastSearch mode (gm_sketch_fastsearch): the rounds' step Delta, else 0
+  int32_t* fs_rounds;     // FastSearch mode: rounds each row took (nullable)
 };
+
+// FastSearch's release (Algorithm 1): an element of weight v in a row of FP64 sum
+// dsum releases the first min(k, ceil(R (v / dsum))) arrivals of its stream by
+// budget R (the ratio and the product in FP64, round to nearest, then the ceiling).
+__device__ __forceinline__ int fs_budget(double R, double v, double dsum, int k) {
+  if (!(R > 0.0)) return 0;
+  const double b = ceil(__dmul_rn(R, __ddiv_rn(v, dsum)));
+  return b < (double)k ? (int)b : k;
+}
 
 
 __device__ __forceinline__ bool positive_finite(double v) {
@@ -137,15 +139,18 @@ __device__ __forceinline__ bool positive_finite(double v) {
 // without a promote list, retagged TAG_SUPER in place.  Updates are idempotent,
 // so a promoted element simply starts again from its first arrival.
 // --------------------------------------------------------------------------
-template <int ARITH, int SW, class PI>
+// BUDGET: FastSearch's release instead of the bound: each claimed element streams
+// exactly its first fs_budget(bR, v, bsum, k) arrivals, all of them kept.
+template <int ARITH, int SW, class PI, bool BUDGET = false>
 __device__ __forceinline__ void seg_phase(const SketchArgs& a, int64_t lo, uint64_t Tbits, Reg* regs,
                                           uint32_t* list, int count, int* cursor, uint32_t want, const PI& pi,
                                           int fill_limit, uint32_t* promote, int* promote_count, Counters& cnt,
-                                          bool& gave_up) {
+                                          bool& gave_up, double bR = 0.0, double bsum = 0.0) {
   constexpr uint32_t SEGM = SW == 32 ? 0xFFFFFFFFu : ((1u << SW) - 1u);
   const int lane = threadIdx.x & 31, sl = lane & (SW - 1), base = lane & ~(SW - 1);
   const int k = a.k;
   int eidx = -1, z0 = 0, fill = 0;
+  int lim = k;  // BUDGET: the element's release
   uint32_t entry = 0u;
   int32_t id = 0;
   double R = 0.0;
@@ -166,7 +171,9 @@ __device__ __forceinline__ void seg_phase(const SketchArgs& a, int64_t lo, uint6
           entry = e;
           const int64_t g = lo + (e & SLOT_MASK);
           id = a.ids[g];
-          R = arr_rcp<ARITH>(a.w[g]);
+          const double v = a.w[g];
+          R = arr_rcp<ARITH>(v);
+          if constexpr (BUDGET) lim = fs_budget(bR, v, bsum, k);
           z0 = 0;
           fill = 0;
           carry = fix_zero();
@@ -181,18 +188,23 @@ __device__ __forceinline__ void seg_phase(const SketchArgs& a, int64_t lo, uint6
     if (!__any_sync(FULL, act)) continue;
     int J;
     const uint64_t bb = seg_batch<ARITH, SW>(act, id, R, z0, k, a.key0, a.key1, a.ctab, carry, lane, J);
-    const uint32_t field = (__ballot_sync(FULL, bb <= Tbits) >> base) & SEGM;
-    const int nkeep = act ? (field == SEGM ? SW : (__ffs(~field) - 1)) : 0;
+    int nkeep;
+    if constexpr (BUDGET) {
+      nkeep = act ? max(0, min(SW, lim - z0)) : 0;
+    } else {
+      const uint32_t field = (__ballot_sync(FULL, bb <= Tbits) >> base) & SEGM;
+      nkeep = act ? (field == SEGM ? SW : (__ffs(~field) - 1)) : 0;
+    }
     if (act && sl == 0) cnt.arrivals += (uint32_t)min(SW, k - z0);
     int c;
     fill += seg_fy_steps<SW>(pi, z0, J, nkeep, lane, c);
-    if (sl < nkeep) {
+    if (sl < nkeep && (!BUDGET || bb <= DBL_MAX_BITS)) {  // a released arrival that is not finite takes no register
       cnt.cas += reg_lower(smem_addr(&regs[c]), bb, (uint64_t)(uint32_t)id, gave_up);
       ++cnt.kept;
     }
     z0 += SW;
     if (act) {
-      if (nkeep < SW || z0 >= k) {
+      if (nkeep < SW || z0 >= k || (BUDGET && z0 >= lim)) {
         eidx = -1;
       } else if (fill > fill_limit) {  // too long for this table: promote
         if (sl == 0) {
@@ -388,6 +400,8 @@ __device__ __forceinline__ void resolve_unit(const SketchArgs& a, uint32_t u, ui
 // MODE_MAIN: all units.  MODE_ESC: the long rows queued for a redo, one CTA each.
 constexpr int MODE_MAIN = 0;
 constexpr int MODE_ESC = 1;
+constexpr int MODE_FS = 2;  // FastSearch's schedule (gm_sketch_fastsearch): every row whole, by one CTA
+constexpr int FS_MAX_ROUNDS = 4096;  // then one last pass releases all k arrivals of every element
 
 
 // C_z = RN(1 / (k - z)); zero the header; check the row_ptr end points.
@@ -524,6 +538,7 @@ __global__ void __launch_bounds__(PREP_THREADS) longprep_kernel(SketchArgs a) {
     int c = 0;
     bool bad = false;
     const bool validate = (a.flags & GM_FLAG_VALIDATE) != 0;
+    const bool fp64_sum = a.r_row != nullptr;  // budget passes only: FP64 adds are slow on GB300
     for (int base = 0; base < n; base += 32 * 8) {  // eight loads in flight per lane, then their sums
       double v[8];
 #pragma unroll
@@ -538,7 +553,7 @@ __global__ void __launch_bounds__(PREP_THREADS) longprep_kernel(SketchArgs a) {
           const float t = s + y;
           comp = (t - s) - y;
           s = t;
-          ds += v[q];
+          if (fp64_sum) ds += v[q];
           ++c;
         } else if (validate) {
           const uint64_t b = (uint64_t)__double_as_longlong(v[q]);
@@ -557,7 +572,7 @@ __global__ void __launch_bounds__(PREP_THREADS) longprep_kernel(SketchArgs a) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
       s += __shfl_xor_sync(FULL, s, d);
-      ds += __shfl_xor_sync(FULL, ds, d);
+      if (fp64_sum) ds += __shfl_xor_sync(FULL, ds, d);
       c += __shfl_xor_sync(FULL, c, d);
     }
     unsigned int last = 0u;
@@ -683,7 +698,8 @@ static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const
                                int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out,
                                void* workspace, size_t workspace_bytes, cudaStream_t stream, bool plain,
                                const float* t_row, const gm_tuning* tuning, const int32_t* init_s = nullptr,
-                               const double* init_y = nullptr, const double* r_row = nullptr);
+                               const double* init_y = nullptr, const double* r_row = nullptr, int fs_delta = 0,
+                               int32_t* fs_rounds = nullptr);
 
 int launch_sketch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows, int64_t nnz,
                   int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out, void* workspace,
@@ -696,8 +712,9 @@ static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const
                                int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t* s_out, double* y_out,
                                void* workspace, size_t workspace_bytes, cudaStream_t stream, bool plain,
                                const float* t_row, const gm_tuning* tuning, const int32_t* init_s,
-                               const double* init_y, const double* r_row) {
+                               const double* init_y, const double* r_row, int fs_delta, int32_t* fs_rounds) {
   const TraceRange trace(plain ? (r_row ? "gm_sketch_budget" : "gm_sketch_plain")
+                               : fs_delta > 0 ? "gm_sketch_fastsearch"
                                : (init_y ? "gm_stream_ingest" : (t_row ? "gm_sketch (per-row bounds)" : "gm_sketch")));
   if (n_rows < 0 || nnz < 0 || k < 1 || k > GM_MAX_K) return GM_EINVAL;
   if (init_y && (n_rows != 1 || plain)) return GM_EINVAL;
@@ -743,6 +760,8 @@ static int launch_sketch_tuned(const int64_t* row_ptr, const int32_t* ids, const
   a.init_s = init_s;
   a.init_y = init_y;
   a.r_row = plain ? r_row : nullptr;
+  a.fs_delta = plain ? 0 : fs_delta;
+  a.fs_rounds = fs_rounds;
   const gm_tuning tn = tuning ? *tuning : tuning_for(k, n_rows, nnz);
   if (!tuning_ok(tn)) return GM_EINVAL;
   a.light_max = tn.light_max;
@@ -1069,6 +1088,17 @@ extern "C" int gm_sketch_budget(const int64_t* row_ptr, const int32_t* ids, cons
                                  flags & (GM_FLAG_VALIDATE | GM_FLAG_FP64_UNIT | GM_FLAG_INT_PRODUCTS), s_out, y_out,
                                  workspace, workspace_bytes, (cudaStream_t)stream, true, nullptr, nullptr, nullptr,
                                  nullptr, R_row);
+}
+
+extern "C" int gm_sketch_fastsearch(const int64_t* row_ptr, const int32_t* ids, const double* w, int32_t n_rows,
+                                    int64_t nnz, int32_t k, uint64_t seed, uint32_t flags, int32_t delta,
+                                    int32_t* rounds_out, int32_t* s_out, double* y_out, void* workspace,
+                                    size_t workspace_bytes, void* stream) {
+  if (delta < 1) return GM_EINVAL;
+  return gm::launch_sketch_tuned(row_ptr, ids, w, n_rows, nnz, k, seed,
+                                 flags & (GM_FLAG_VALIDATE | GM_FLAG_FP64_UNIT | GM_FLAG_INT_PRODUCTS), s_out, y_out,
+                                 workspace, workspace_bytes, (cudaStream_t)stream, false, nullptr, nullptr, nullptr,
+                                 nullptr, nullptr, delta, rounds_out);
 }
 
 extern "C" size_t gm_sketch_bounded_workspace_bytes(int32_t n_rows, int64_t nnz, int32_t k) {

@@ -124,6 +124,10 @@ def lib():
         L.gm_sketch_bounded.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                         ctypes.c_uint32, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
         L.gm_row_ystar.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
+        L.gm_sketch_fastsearch.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                           ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                           ctypes.c_size_t, _vp]
+        L.gm_sketch_noalloc_status.argtypes = [ctypes.POINTER(gm_stats), _vp]
         L.gm_sketch_host_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
         L.gm_sketch_host_workspace_bytes.restype = ctypes.c_size_t
         L.gm_sketch_host_workspace_bytes_csr.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
@@ -536,6 +540,20 @@ def gm_sketch_bounded(row_ptr, ids, w, k, seed, bound_row, flags=0, s_out=None, 
                          device=row_ptr.device)
     fn = lambda *a: lib().gm_sketch_bounded(*a[:8], _ptr(bound_row), *a[8:])
     return _sketch(fn, "gm_sketch_bounded", row_ptr, ids, w, k, seed, flags, s_out, y_out, ws, stream)
+
+
+def gm_sketch_fastsearch(row_ptr, ids, w, k, seed, delta=None, flags=0, rounds_out=None, s_out=None, y_out=None,
+                         ws=None, stream=None):
+    """FastGM under the paper's FastSearch schedule, all rounds on the device
+    (Algorithm 1; delta defaults to k) -> (s, y, workspace, rounds int32 [n_rows])."""
+    n_rows = row_ptr.numel() - 1
+    delta = int(delta or k)
+    if rounds_out is None:
+        rounds_out = torch.zeros(n_rows, dtype=torch.int32, device=row_ptr.device)
+    _need_cuda(rounds_out, torch.int32, "rounds_out")
+    fn = lambda *a: lib().gm_sketch_fastsearch(*a[:8], delta, _ptr(rounds_out), *a[8:])
+    s, y, ws = _sketch(fn, "gm_sketch_fastsearch", row_ptr, ids, w, k, seed, flags, s_out, y_out, ws, stream)
+    return s, y, ws, rounds_out
 
 
 def gm_row_ystar(y, out=None, stream=None):

@@ -1,7 +1,8 @@
-"""The paper's FastSearch schedule on the GPU (gm_sketch_budget, gm_sketch_bounded):
-its budgets, rounds and released arrivals equal the oracle's Algorithm 1 when the
-row sums are exact in any order (dyadic weights), and FastSearch + FastPrune give
-gm_sketch's registers; caller-given bounds of any value give them too."""
+"""The paper's FastSearch schedule on the GPU (gm_sketch_fastsearch, gm_sketch_budget,
+gm_sketch_bounded): its rounds and released arrivals equal the oracle's Algorithm 1
+when the row sums are exact in any order (dyadic weights), and FastSearch +
+FastPrune give gm_sketch's registers; caller-given bounds of any value give them
+too."""
 import numpy as np
 import pytest
 import torch
@@ -27,19 +28,38 @@ def dyadic_rows(seed, lens):
 
 @pytest.mark.parametrize("k,delta", [(16, 16), (64, 64), (256, 100)])
 def test_fastsearch_matches_algorithm_1(k, delta):
-    X = dyadic_rows(k, [1, 3, 40, 200, 900, 40000])  # the last one spans two chunks
+    """The device schedule (gm_sketch_fastsearch) takes, for every row, the rounds
+    Algorithm 1 takes, and gives gm_sketch's registers; the budgets of its last
+    round release the arrivals Algorithm 1's FastSearch released."""
+    X = dyadic_rows(k, [1, 3, 40, 200, 900, 40000])  # the last one longer than a chunk
     rp, ids, w = gm.to_device(X)
     s, y, info = fastsearch.fastsearch_sketch(rp, ids, w, k, 7, delta=delta)
     s0, y0, _ = gm.gm_sketch(rp, ids, w, k, 7)
     assert torch.equal(s, s0) and torch.equal(y.view(torch.int64), y0.view(torch.int64))
-    R = info["R"].cpu().numpy()
+    rounds = info["rounds"].cpu().numpy()
+    R_dev = torch.zeros(X.n_rows, dtype=torch.float64, device="cuda")
     total = 0
     for r in range(X.n_rows):
         lo, hi = X.row_ptr[r], X.row_ptr[r + 1]
         _, _, _, R_alg, arr_alg = oracle.fastgm_alg1(X.ids[lo:hi], X.w[lo:hi], k, 7, delta=delta, search=True)
-        assert R[r] == R_alg, (r, R[r], R_alg)
+        assert rounds[r] * delta == R_alg, (r, rounds[r], R_alg)
+        R_dev[r] = float(R_alg)
         total += arr_alg
-    assert info["search_arrivals"] == total
+    # the release step alone at those budgets (gm_sketch_budget) fills every register
+    # with the arrivals Algorithm 1 released
+    sb, yb, wsb = gm.gm_sketch_budget(rp, ids, w, k, 7, R_dev)
+    assert gm.gm_status(wsb)[1]["arrivals"] == total
+    assert bool(torch.isfinite(yb).all())
+
+
+def test_fastsearch_on_lognormal_rows():
+    """Non-dyadic weights, k = 1024: the same registers as gm_sketch, rounds > 1."""
+    X = W.lognormal_batch(seed=31, n_rows=48, median=1500.0, hi=40000)
+    rp, ids, w = gm.to_device(X)
+    s, y, info = fastsearch.fastsearch_sketch(rp, ids, w, 1024, 5)
+    s0, y0, _ = gm.gm_sketch(rp, ids, w, 1024, 5)
+    assert torch.equal(s, s0) and torch.equal(y.view(torch.int64), y0.view(torch.int64))
+    assert info["max_rounds"] > 1 and bool((info["rounds"] >= 1).all())
 
 
 def test_bounds_of_any_value_give_the_same_registers():
