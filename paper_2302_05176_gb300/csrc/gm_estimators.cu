@@ -25,24 +25,22 @@ static int timed_launch(cudaStream_t st, F launch) {
   return cudaGetLastError() == cudaSuccess ? GM_OK : GM_ECUDA;
 }
 
-// One CTA per pair: count equal, filled registers.
-__global__ void __launch_bounds__(EST_BLOCK) jaccard_kernel(const int32_t* __restrict__ sa,
-                                                             const int32_t* __restrict__ sb, int64_t n_pairs, int k,
-                                                             double* __restrict__ out) {
-  __shared__ int red[EST_BLOCK / 32];
-  for (int64_t p = blockIdx.x; p < n_pairs; p += gridDim.x) {
-    const double j = block_jaccard<EST_BLOCK>(sa + p * k, sb + p * k, k, red);
-    if (threadIdx.x == 0) out[p] = j;
+// One warp per pair: count equal, filled registers.
+__global__ void jaccard_kernel(const int32_t* __restrict__ sa, const int32_t* __restrict__ sb, int64_t n_pairs,
+                               int k, double* __restrict__ out) {
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); p < n_pairs; p += warps) {
+    const double j = warp_jaccard(sa + p * k, sb + p * k, k);
+    if ((threadIdx.x & 31) == 0) out[p] = j;
   }
 }
 
-// One CTA per row: (k - 1) / sum of the registers.
-__global__ void __launch_bounds__(EST_BLOCK) cardinality_kernel(const double* __restrict__ y, int n_rows, int k,
-                                                                 double* __restrict__ out) {
-  __shared__ unsigned long long red[2 * (EST_BLOCK / 32)];
-  for (int64_t r = blockIdx.x; r < n_rows; r += gridDim.x) {
-    const double c = block_cardinality<EST_BLOCK>(y + r * k, k, red);
-    if (threadIdx.x == 0) out[r] = c;
+// One warp per row: (k - 1) / sum of the registers.
+__global__ void cardinality_kernel(const double* __restrict__ y, int n_rows, int k, double* __restrict__ out) {
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); r < n_rows; r += warps) {
+    const double c = warp_cardinality(y + r * k, k);
+    if ((threadIdx.x & 31) == 0) out[r] = c;
   }
 }
 
@@ -78,7 +76,8 @@ extern "C" int gm_jaccard(const int32_t* s_a, const int32_t* s_b, int64_t n_pair
   if (!s_a || !s_b || !out) return GM_EINVAL;
   const cudaStream_t st = (cudaStream_t)stream;
   return gm::timed_launch(st, [&] {
-    gm::jaccard_kernel<<<gm::grid_for(n_pairs, 1), gm::EST_BLOCK, 0, st>>>(s_a, s_b, n_pairs, k, out);
+    gm::jaccard_kernel<<<gm::grid_for(n_pairs, gm::EST_BLOCK / 32), gm::EST_BLOCK, 0, st>>>(s_a, s_b, n_pairs, k,
+                                                                                             out);
   });
 }
 
@@ -88,7 +87,7 @@ extern "C" int gm_cardinality(const double* y, int32_t n_rows, int32_t k, double
   if (!y || !out) return GM_EINVAL;
   const cudaStream_t st = (cudaStream_t)stream;
   return gm::timed_launch(st, [&] {
-    gm::cardinality_kernel<<<gm::grid_for(n_rows, 1), gm::EST_BLOCK, 0, st>>>(y, n_rows, k, out);
+    gm::cardinality_kernel<<<gm::grid_for(n_rows, gm::EST_BLOCK / 32), gm::EST_BLOCK, 0, st>>>(y, n_rows, k, out);
   });
 }
 
