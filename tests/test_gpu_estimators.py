@@ -1,8 +1,8 @@
 """gm_cardinality's sum on adversarial register values (GPU), against the
 correctly rounded sum of Python's math.fsum: the estimate (k - 1) / sum y must
-agree within k 2^-52 relative (the documented bound of any summation order; the
-library's sum is within k 2^-60 of the correctly rounded one), and the same row
-must give the same bits on every call."""
+agree within k 2^-52 relative (the documented bound of an FP64 sum of k
+non-negative terms in any order), and the same row must give the same bits on
+every call."""
 import math
 
 import numpy as np
