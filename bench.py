@@ -1009,7 +1009,7 @@ def serving_leg(args):
     finally:
         gc.enable()
     keys = ("throughput_rps", "p50_ms", "p99_ms", "max_ms", "sketch_p99_ms", "query_p99_ms", "mean_batch_rows",
-            "late_submits", "worst_window")
+            "late_submits", "worst_window", "slowest")
     out = {"requests": runs[0]["requests"], "sketches": runs[0]["sketches"], "queries": runs[0]["queries"],
            "distinct_vectors": len(pinned), "elements": runs[0]["elements"], "offered_rate_rps": SERVE_RATE,
            "span_s": runs[0]["span_s"], "generate_s": gen_s,
@@ -1056,13 +1056,16 @@ def _serve_once(args, reqs, bufs, burst=False):
         lat = {"sketch": [], "jaccard": [], "cardinality": []}
         last = start
         batch = []
-        every_lat, every_due = [], []
+        every_lat, every_due, slow = [], [], []
         for i, r in enumerate(reqs):
             rc, res = srv.wait(tick[i], 600.0)
             if rc != 0:
                 raise RuntimeError("serving request %d failed: %d" % (i, rc))
             lat[r.kind].append((res["t_done_ns"] - due[i]) / 1e6)
             every_lat.append((res["t_done_ns"] - due[i]) / 1e6)
+            slow.append(((res["t_done_ns"] - due[i]) / 1e6, (due[i] - start) / 1e9, r.kind, r.k,
+                         r.csr.nnz if r.kind == "sketch" else 0, (res["t_launch_ns"] - due[i]) / 1e6,
+                         res["batch_size"]))
             every_due.append((due[i] - start) / 1e9)
             last = max(last, res["t_done_ns"])
             if r.kind == "sketch":
@@ -1089,6 +1092,8 @@ def _serve_once(args, reqs, bufs, burst=False):
             "elements_per_s": nnz / span, "elements": nnz,
             "p50_ms": pct(every, 50), "p99_ms": pct(every, 99), "max_ms": float(every.max()) if every.size else None,
             "late_submits": late, "worst_window": worst,
+            "slowest": [{"ms": a, "arrive_s": b, "kind": c, "k": d, "nnz": e, "wait_to_launch_ms": f, "batch": g}
+                        for a, b, c, d, e, f, g in sorted(slow, reverse=True)[:6]],
             "sketch_p50_ms": pct(lat["sketch"], 50), "sketch_p99_ms": pct(lat["sketch"], 99),
             "query_p50_ms": pct(lat["jaccard"] + lat["cardinality"], 50),
             "query_p99_ms": pct(lat["jaccard"] + lat["cardinality"], 99),
