@@ -879,7 +879,7 @@ static int launch_all(SketchArgs a, bool plain, int nsm, cudaStream_t stream) {
   // Long rows are cut into SPLIT_LEN-element chunks.  (16,384-element chunks,
   // for more units per CTA, made the 16 x 10^6 Pareto launch slower: 0.478 against
   // 0.40 ms; each unit's phase barriers and merge cost more than the balance gained.)
-  a.chunk_len = SPLIT_LEN;
+  a.chunk_len = GM_CHUNK_LEN;
   const int max_units = a.n_rows + (int)((a.nnz + a.chunk_len - 1) / a.chunk_len) + a.max_long;
   if (a.fs_delta == 0) {  // FastSearch's schedule takes every row whole: no long-row plan
     plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);

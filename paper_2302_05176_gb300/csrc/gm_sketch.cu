@@ -57,6 +57,10 @@ namespace gm {
 #ifndef GM_MED_SW
 #define GM_MED_SW 8
 #endif
+// Elements per chunk of a long row (rows longer than SPLIT_LEN are cut into chunks).
+#ifndef GM_CHUNK_LEN
+#define GM_CHUNK_LEN 32768
+#endif
 // Default routing by the expected number of arrivals below T (gm_tuning): light
 // lanes up to LIGHT_MAX, 8-lane segments up to MEDIUM_MAX, 32-lane warps up to
 // HEAVY_MAX, dense permutations beyond; first-pass bound at quantile 1 - P_FIRST.
