@@ -876,10 +876,11 @@ template <int ARITH>
 static int launch_all(SketchArgs a, bool plain, int nsm, cudaStream_t stream) {
   const size_t sm = plain ? plain_smem_bytes(a.k) : fast_smem_bytes(a.k, a.ndense);
   int grid = 0, rc;
-  // Long rows are cut into SPLIT_LEN-element chunks.  (16,384-element chunks,
-  // for more units per CTA, made the 16 x 10^6 Pareto launch slower: 0.478 against
-  // 0.40 ms; each unit's phase barriers and merge cost more than the balance gained.)
-  a.chunk_len = GM_CHUNK_LEN;
+  // Long rows are cut into GM_CHUNK_LEN-element chunks (measured: see its definition).
+  // The plain sketch keeps SPLIT_LEN-element chunks: every element costs k arrivals
+  // there, so a 64K chunk on one CTA would set the launch's tail (0.49 s against
+  // 0.41 s at k = 1024 on the lognormal batch).
+  a.chunk_len = plain ? SPLIT_LEN : GM_CHUNK_LEN;
   const int max_units = a.n_rows + (int)((a.nnz + a.chunk_len - 1) / a.chunk_len) + a.max_long;
   if (a.fs_delta == 0) {  // FastSearch's schedule takes every row whole: no long-row plan
     plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);
