@@ -872,15 +872,38 @@ static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
   return GM_OK;
 }
 
+// Elements per chunk of a long row for a launch of `grid` persistent CTAs: about
+// 1.75 units per CTA if the batch were all long rows, in whole 4,096-element
+// steps, between 8,192 and GM_CHUNK_LEN.  A batch of many long rows gets large
+// chunks (each unit pays phase barriers, the tails of its heavy elements and a
+// merge: 16 x 10^6 Pareto(1.2) at k = 4096, per main-kernel launch: 32K chunks 0.400
+// ms, 48K 0.383, 64K 0.373, 112K 0.426); a single long row (a Stream-FastGM chunk
+// of 10^6 items) gets small ones, so that its units still fill the grid.
+static int chunk_len_for(int64_t nnz, int grid) {
+  int64_t c = (int64_t)((double)nnz / (1.75 * (double)(grid > 0 ? grid : 1)));
+  c = (c + 4095) / 4096 * 4096;
+  if (c < 8192) c = 8192;
+  if (c > GM_CHUNK_LEN) c = GM_CHUNK_LEN;
+  return (int)c;
+}
+
 template <int ARITH>
 static int launch_all(SketchArgs a, bool plain, int nsm, cudaStream_t stream) {
   const size_t sm = plain ? plain_smem_bytes(a.k) : fast_smem_bytes(a.k, a.ndense);
   int grid = 0, rc;
-  // Long rows are cut into GM_CHUNK_LEN-element chunks (measured: see its definition).
   // The plain sketch keeps SPLIT_LEN-element chunks: every element costs k arrivals
   // there, so a 64K chunk on one CTA would set the launch's tail (0.49 s against
   // 0.41 s at k = 1024 on the lognormal batch).
-  a.chunk_len = plain ? SPLIT_LEN : GM_CHUNK_LEN;
+  if (plain) {
+    a.chunk_len = SPLIT_LEN;
+  } else {
+    int per_sm = 0;
+    if (allow_max_smem((const void*)fastgm_kernel<ARITH, MODE_MAIN>) != GM_OK) return GM_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fastgm_kernel<ARITH, MODE_MAIN>, BLOCK, sm) !=
+        cudaSuccess)
+      return GM_ECUDA;
+    a.chunk_len = chunk_len_for(a.nnz, nsm * (per_sm > 0 ? per_sm : 1));
+  }
   const int max_units = a.n_rows + (int)((a.nnz + a.chunk_len - 1) / a.chunk_len) + a.max_long;
   if (a.fs_delta == 0) {  // FastSearch's schedule takes every row whole: no long-row plan
     plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);

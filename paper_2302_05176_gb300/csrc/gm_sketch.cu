@@ -57,10 +57,8 @@ namespace gm {
 #ifndef GM_MED_SW
 #define GM_MED_SW 8
 #endif
-// Elements per chunk of a long row (rows longer than SPLIT_LEN are cut into
-// chunks).  Measured on 16 x 10^6 Pareto(1.2) at k = 4096: 32K 0.400 ms, 48K 0.383,
-// 64K 0.373, 112K 0.426 per main-kernel launch (each unit pays phase tails, a merge
-// and barriers; too few units leave SMs idle); the lognormal batch is unaffected.
+// The largest chunk of a long row (rows longer than SPLIT_LEN are cut into chunks
+// of a length chosen per launch, chunk_len_for).
 #ifndef GM_CHUNK_LEN
 #define GM_CHUNK_LEN 65536
 #endif
