@@ -27,9 +27,11 @@ __host__ __device__ inline size_t fast_area_bytes() {
   size_t m = maps > hashes ? maps : hashes;
   return m > med ? m : med;
 }
-// Per-warp screening buffer of the light path: the survivors of a 32-element
-// screening batch with their 1/v and id (doubles first: 8-byte aligned).
-constexpr size_t WBUF_BYTES = 32 * 8 + 32 * 4 + 32 * 4;
+// Per-warp screening buffer of the light path: the survivors of a screening
+// batch (32 elements, or 64 when long-row chunks screen two per lane) with their
+// 1/v and id (doubles first: 8-byte aligned).
+constexpr int WB_N = 32 * GM_SCREEN_PAIR;
+constexpr size_t WBUF_BYTES = (size_t)WB_N * (8 + 4 + 4);
 __host__ __device__ inline size_t fast_smem_bytes(int k, int ndense) {
   return (size_t)k * sizeof(Reg) + fast_area_bytes() + (size_t)ndense * pi_stride(k) * 2 + (size_t)WARPS * WBUF_BYTES;
 }
@@ -43,6 +45,34 @@ __host__ __device__ inline size_t plain_smem_bytes(int k) {
 // as an FP32 value (equal as reals).  Elements expected to need more than
 // a.light_max arrivals go to the work list, tagged by their expected count.
 // --------------------------------------------------------------------------
+// The screen of one element of a batch (slot < n): positive weights are counted,
+// routed to the work list by their expected arrivals below T, or screened by
+// their first arrival; surv = it takes a light lane.
+// The id is loaded here when `load_id` (a batch loaded at the screen), else given.
+__device__ __forceinline__ void screen_elem(const SketchArgs& a, int64_t lo, int n, int slot, double v, int32_t& idv,
+                                            bool load_id, float Tf, float kf, SmemScalars& sh, Counters& cnt,
+                                            bool& surv) {
+  if (!positive_finite(v)) return;
+  ++cnt.elements;
+  const float vf = f32_trunc(v);
+  const float lam = kf * (1.0f - __expf(-(vf * Tf)));  // expected arrivals <= T (routing only)
+  if (lam > a.light_max) {
+    // 8-lane work from the front of the unit's list, 32-lane and dense work from
+    // its back: each warp phase scans only its own class
+    if (lam > a.medium_max)
+      a.list[lo + n - 1 - atomicAdd(&sh.bcount, 1)] = (uint32_t)slot | (lam > a.heavy_max ? TAG_SUPER : TAG_HEAVY);
+    else
+      a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | TAG_MEDIUM;
+  } else {
+    if (load_id) idv = a.ids[lo + slot];
+    const Words wd = philox((uint32_t)idv, 0u, a.key0, a.key1);
+    if (screen_out(wd.w1, vf, Tf, kf))
+      ++cnt.screened;  // first arrival certainly above T: nothing of it counts
+    else
+      surv = true;
+  }
+}
+
 // PF: claim and load each screening batch one batch ahead (long-row chunks, whose
 // elements come from HBM); without it a batch is loaded when it is screened
 // (short rows, whose weights the row sum has just brought into L2).
@@ -51,9 +81,9 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
                                             Reg* regs, uint32_t* map, unsigned char* wbuf, SmemScalars& sh,
                                             Counters& cnt, bool& gave_up) {
   const int tid = threadIdx.x, lane = tid & 31;
-  double* wb_r = reinterpret_cast<double*>(wbuf);            // 1/v of each survivor
-  uint32_t* wb_slot = reinterpret_cast<uint32_t*>(wbuf + 256);  // its slot in the unit
-  int32_t* wb_id = reinterpret_cast<int32_t*>(wbuf + 384);     // its id
+  double* wb_r = reinterpret_cast<double*>(wbuf);                 // 1/v of each survivor
+  uint32_t* wb_slot = reinterpret_cast<uint32_t*>(wbuf + WB_N * 8);  // its slot in the unit
+  int32_t* wb_id = reinterpret_cast<int32_t*>(wbuf + WB_N * 12);     // its id
   const int k = a.k;
   const float kf = (float)k;
   int e = -1, z = 0, msize = 0;
@@ -62,17 +92,23 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
   Fix acc = fix_zero();
   int wcount = 0;
   bool pool_done = false;
-  // the warp's next screening batch, claimed and loaded one batch ahead so that its
+  // the warp's next screening batch (PB elements, two per lane when GM_SCREEN_PAIR
+  // is 2: independent Philox chains), claimed and loaded one batch ahead so that its
   // weight and id loads are in flight while the current batch is screened
+  constexpr int PB = PF ? 32 * GM_SCREEN_PAIR : 32;
   int nbase = 0;
-  double nv = 0.0;
-  int32_t nid = 0;
+  double nv = 0.0, nv2 = 0.0;
+  int32_t nid = 0, nid2 = 0;
   if (PF) {
-    if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
+    if (lane == 0) nbase = atomicAdd(&sh.pool, PB);
     nbase = __shfl_sync(FULL, nbase, 0);
     if (nbase + lane < n) {
       nv = __ldcs(a.w + lo + nbase + lane);
       nid = __ldcs(a.ids + lo + nbase + lane);
+    }
+    if (PB == 64 && nbase + 32 + lane < n) {
+      nv2 = __ldcs(a.w + lo + nbase + 32 + lane);
+      nid2 = __ldcs(a.ids + lo + nbase + 32 + lane);
     }
   }
   while (true) {
@@ -81,12 +117,14 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
     while (nmask && !(pool_done && wcount == 0)) {
       if (wcount == 0) {
         int base = 0;
-        double v = 0.0;
-        int32_t idv = 0;
+        double v = 0.0, v2 = 0.0;
+        int32_t idv = 0, idv2 = 0;
         if (PF) {
           base = nbase;
           v = nv;
           idv = nid;
+          v2 = nv2;
+          idv2 = nid2;
         } else {
           if (lane == 0) base = atomicAdd(&sh.pool, 32);
           base = __shfl_sync(FULL, base, 0);
@@ -95,40 +133,25 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
           pool_done = true;
           break;
         }
-        const int slot = base + lane;
-        bool surv = false;
+        const int slot = base + lane, slot2 = base + 32 + lane;
+        bool surv = false, surv2 = false;
         if (PF) {
-          if (lane == 0) nbase = atomicAdd(&sh.pool, 32);
+          if (lane == 0) nbase = atomicAdd(&sh.pool, PB);
           nbase = __shfl_sync(FULL, nbase, 0);
           if (nbase + lane < n) {
             nv = __ldcs(a.w + lo + nbase + lane);
             nid = __ldcs(a.ids + lo + nbase + lane);
           }
+          if (PB == 64 && nbase + 32 + lane < n) {
+            nv2 = __ldcs(a.w + lo + nbase + 32 + lane);
+            nid2 = __ldcs(a.ids + lo + nbase + 32 + lane);
+          }
         }
         if (slot < n) {
           if (!PF) v = a.w[lo + slot];
-          if (positive_finite(v)) {
-            ++cnt.elements;
-            const float vf = f32_trunc(v);
-            const float lam = kf * (1.0f - __expf(-(vf * Tf)));  // expected arrivals <= T (routing only)
-            if (lam > a.light_max) {
-              // 8-lane work from the front of the unit's list, 32-lane and dense work from
-              // its back: each warp phase scans only its own class
-              if (lam > a.medium_max)
-                a.list[lo + n - 1 - atomicAdd(&sh.bcount, 1)] =
-                    (uint32_t)slot | (lam > a.heavy_max ? TAG_SUPER : TAG_HEAVY);
-              else
-                a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | TAG_MEDIUM;
-            } else {
-              if (!PF) idv = a.ids[lo + slot];
-              const Words wd = philox((uint32_t)idv, 0u, a.key0, a.key1);
-              if (screen_out(wd.w1, vf, Tf, kf))
-                ++cnt.screened;  // first arrival certainly above T: nothing of it counts
-              else
-                surv = true;
-            }
-          }
+          screen_elem(a, lo, n, slot, v, idv, !PF, Tf, kf, sh, cnt, surv);
         }
+        if (PB == 64 && slot2 < n) screen_elem(a, lo, n, slot2, v2, idv2, false, Tf, kf, sh, cnt, surv2);
         const uint32_t sm = __ballot_sync(FULL, surv);
         if (surv) {  // one reciprocal per screening batch, not one per lane refill
           const int p = __popc(sm & lanemask_lt());
@@ -137,6 +160,16 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
           wb_id[p] = idv;
         }
         wcount = __popc(sm);
+        if (PB == 64) {
+          const uint32_t sm2 = __ballot_sync(FULL, surv2);
+          if (surv2) {
+            const int p = wcount + __popc(sm2 & lanemask_lt());
+            wb_r[p] = arr_rcp<ARITH>(v2);
+            wb_slot[p] = (uint32_t)slot2;
+            wb_id[p] = idv2;
+          }
+          wcount += __popc(sm2);
+        }
         __syncwarp();
         continue;
       }
@@ -223,8 +256,8 @@ __device__ __forceinline__ void budget_light_phase(const SketchArgs& a, int64_t 
                                                    SmemScalars& sh, Counters& cnt, bool& gave_up) {
   const int tid = threadIdx.x, lane = tid & 31;
   double* wb_r = reinterpret_cast<double*>(wbuf);
-  uint32_t* wb_slot = reinterpret_cast<uint32_t*>(wbuf + 256);
-  int32_t* wb_id = reinterpret_cast<int32_t*>(wbuf + 384);
+  uint32_t* wb_slot = reinterpret_cast<uint32_t*>(wbuf + WB_N * 8);
+  int32_t* wb_id = reinterpret_cast<int32_t*>(wbuf + WB_N * 12);
   const int k = a.k;
   int e = -1, z = 0, msize = 0, lim = 0;
   int32_t id = 0;
@@ -880,7 +913,7 @@ static int occupancy_grid(KERNEL kern, size_t sm, int nsm, int cap, int& grid) {
 // ms, 48K 0.383, 64K 0.373, 112K 0.426); a single long row (a Stream-FastGM chunk
 // of 10^6 items) gets small ones, so that its units still fill the grid.
 static int chunk_len_for(int64_t nnz, int grid) {
-  int64_t c = (int64_t)((double)nnz / (1.75 * (double)(grid > 0 ? grid : 1)));
+  int64_t c = (int64_t)((double)nnz / (GM_CHUNK_UNITS_PER_CTA * (double)(grid > 0 ? grid : 1)));
   c = (c + 4095) / 4096 * 4096;
   if (c < 8192) c = 8192;
   if (c > GM_CHUNK_LEN) c = GM_CHUNK_LEN;

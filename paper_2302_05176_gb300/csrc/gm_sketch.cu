@@ -62,6 +62,14 @@ namespace gm {
 #ifndef GM_CHUNK_LEN
 #define GM_CHUNK_LEN 65536
 #endif
+// Elements each lane screens per batch in long-row chunks (1 or 2).
+#ifndef GM_SCREEN_PAIR
+#define GM_SCREEN_PAIR 1
+#endif
+// Long-row chunk units per CTA of the persistent grid that chunk_len_for aims at.
+#ifndef GM_CHUNK_UNITS_PER_CTA
+#define GM_CHUNK_UNITS_PER_CTA 1.75
+#endif
 // Default routing by the expected number of arrivals below T (gm_tuning): light
 // lanes up to LIGHT_MAX, 8-lane segments up to MEDIUM_MAX, 32-lane warps up to
 // HEAVY_MAX, dense permutations beyond; first-pass bound at quantile 1 - P_FIRST.
