@@ -52,6 +52,22 @@ def test_fastsearch_matches_algorithm_1(k, delta):
     assert bool(torch.isfinite(yb).all())
 
 
+def test_fastsearch_wide_shape_k4096():
+    """k = 4096 runs the schedule on 1024-thread CTAs: rounds equal Algorithm 1's,
+    registers equal gm_sketch's, on dyadic rows including one of 40,000 elements."""
+    k, delta = 4096, 4096
+    X = dyadic_rows(99, [2, 50, 700, 3000, 40000])
+    rp, ids, w = gm.to_device(X)
+    s, y, info = fastsearch.fastsearch_sketch(rp, ids, w, k, 11, delta=delta)
+    s0, y0, _ = gm.gm_sketch(rp, ids, w, k, 11)
+    assert torch.equal(s, s0) and torch.equal(y.view(torch.int64), y0.view(torch.int64))
+    rounds = info["rounds"].cpu().numpy()
+    for r in range(X.n_rows):
+        lo, hi = X.row_ptr[r], X.row_ptr[r + 1]
+        _, _, _, R_alg, _ = oracle.fastgm_alg1(X.ids[lo:hi], X.w[lo:hi], k, 11, delta=delta, search=True)
+        assert rounds[r] * delta == R_alg, (r, rounds[r], R_alg)
+
+
 def test_fastsearch_on_lognormal_rows():
     """Non-dyadic weights, k = 1024: the same registers as gm_sketch, rounds > 1."""
     X = W.lognormal_batch(seed=31, n_rows=48, median=1500.0, hi=40000)
