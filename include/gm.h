@@ -164,7 +164,7 @@ int gm_sketch_plain(const int64_t* row_ptr, const int32_t* ids, const double* w,
  *
  * The scratch is one fixed device array inside libgm, sized for
  * nnz <= GM_NOALLOC_MAX_NNZ, n_rows <= GM_NOALLOC_MAX_ROWS and k <= GM_MAX_K:
- * 10,787,584 bytes (about 10.8 MB) that every GPU which loads the library holds
+ * 10,788,096 bytes (about 10.8 MB) that every GPU which loads the library holds
  * until the process exits.  Arguments and output are those of gm_sketch (same
  * kernels, same registers), minus the workspace.
  *   - Returns GM_ENOMEM if nnz > GM_NOALLOC_MAX_NNZ or n_rows >

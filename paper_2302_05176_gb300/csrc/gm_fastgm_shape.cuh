@@ -9,6 +9,12 @@ constexpr int BLOCK = GM_SHAPE_BLOCK;
 constexpr int WARPS = BLOCK / 32;
 constexpr int CTAS_PER_SM = 1024 / BLOCK;
 constexpr int MAPCAP = GM_MAPCAP;  // displaced positions a light lane can track
+// The 512-thread shape compiles the compacted units into its one main kernel
+// (taken by a runtime flag); the 1024-thread shape into a second instance
+// (MODE_CMP), so that its main kernel keeps the register allocation of the
+// short-row path.  Both were measured against the other choice (k = 1024:
+// 2.57 against 2.64 ms; k = 4096: 8.60 against 8.68 ms per main kernel).
+constexpr bool SHARED_CMP = BLOCK == 512;
 
 struct SmemScalars {
   int pool, hcount, bcount, pcount, c_med, c_heavy, c_pheavy, c_super, c_psuper, unit, last;
@@ -49,9 +55,10 @@ __host__ __device__ inline size_t plain_smem_bytes(int k) {
 // routed to the work list by their expected arrivals below T, or screened by
 // their first arrival; surv = it takes a light lane.
 // The id is loaded here when `load_id` (a batch loaded at the screen), else given.
-__device__ __forceinline__ void screen_elem(const SketchArgs& a, int64_t lo, int n, int slot, double v, int32_t& idv,
-                                            bool load_id, float Tf, float kf, SmemScalars& sh, Counters& cnt,
-                                            bool& surv) {
+// `slot` is the element's offset from lo; the unit's work list starts at list + lb.
+__device__ __forceinline__ void screen_elem(const SketchArgs& a, int64_t lo, int64_t lb, int n, int slot, double v,
+                                            int32_t& idv, bool load_id, float Tf, float kf, SmemScalars& sh,
+                                            Counters& cnt, bool& surv) {
   if (!positive_finite(v)) return;
   ++cnt.elements;
   const float vf = f32_trunc(v);
@@ -60,9 +67,9 @@ __device__ __forceinline__ void screen_elem(const SketchArgs& a, int64_t lo, int
     // 8-lane work from the front of the unit's list, 32-lane and dense work from
     // its back: each warp phase scans only its own class
     if (lam > a.medium_max)
-      a.list[lo + n - 1 - atomicAdd(&sh.bcount, 1)] = (uint32_t)slot | (lam > a.heavy_max ? TAG_SUPER : TAG_HEAVY);
+      a.list[lb + n - 1 - atomicAdd(&sh.bcount, 1)] = (uint32_t)slot | (lam > a.heavy_max ? TAG_SUPER : TAG_HEAVY);
     else
-      a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | TAG_MEDIUM;
+      a.list[lb + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | TAG_MEDIUM;
   } else {
     if (load_id) idv = a.ids[lo + slot];
     const Words wd = philox((uint32_t)idv, 0u, a.key0, a.key1);
@@ -76,10 +83,14 @@ __device__ __forceinline__ void screen_elem(const SketchArgs& a, int64_t lo, int
 // PF: claim and load each screening batch one batch ahead (long-row chunks, whose
 // elements come from HBM); without it a batch is loaded when it is screened
 // (short rows, whose weights the row sum has just brought into L2).
+// ind (with PF): the unit's n elements are the entries plist[lb, lb + n) of a
+// compacted long row, offsets from lo; otherwise elements [lo, lo + n) (lb = lo).
+// The unit's work list is list[lb, lb + n) either way.
 template <int ARITH, bool PF>
-__device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int n, uint64_t Tbits, float Tf,
-                                            Reg* regs, uint32_t* map, unsigned char* wbuf, SmemScalars& sh,
-                                            Counters& cnt, bool& gave_up) {
+__device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int64_t lb, int n, uint64_t Tbits,
+                                            float Tf, Reg* regs, uint32_t* map, unsigned char* wbuf, SmemScalars& sh,
+                                            Counters& cnt, bool& gave_up, bool ind = false) {
+  const bool IND = PF && ind;
   const int tid = threadIdx.x, lane = tid & 31;
   double* wb_r = reinterpret_cast<double*>(wbuf);                 // 1/v of each survivor
   uint32_t* wb_slot = reinterpret_cast<uint32_t*>(wbuf + WB_N * 8);  // its slot in the unit
@@ -95,16 +106,23 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
   // the warp's next screening batch (PB elements, two per lane when GM_SCREEN_PAIR
   // is 2: independent Philox chains), claimed and loaded one batch ahead so that its
   // weight and id loads are in flight while the current batch is screened
-  constexpr int PB = PF ? 32 * GM_SCREEN_PAIR : 32;
+  constexpr int PB = PF ? 32 * GM_SCREEN_PAIR : 32;  // compacted units: GM_SCREEN_PAIR is 1
   int nbase = 0;
   double nv = 0.0, nv2 = 0.0;
   int32_t nid = 0, nid2 = 0;
+  int nslot = 0;  // IND: the next batch's element offsets
   if (PF) {
     if (lane == 0) nbase = atomicAdd(&sh.pool, PB);
     nbase = __shfl_sync(FULL, nbase, 0);
     if (nbase + lane < n) {
-      nv = __ldcs(a.w + lo + nbase + lane);
-      nid = __ldcs(a.ids + lo + nbase + lane);
+      if (IND) {
+        nslot = (int)__ldcs(a.plist + lb + nbase + lane);
+        nv = __ldcs(a.w + lo + nslot);
+        nid = __ldcs(a.ids + lo + nslot);
+      } else {
+        nv = __ldcs(a.w + lo + nbase + lane);
+        nid = __ldcs(a.ids + lo + nbase + lane);
+      }
     }
     if (PB == 64 && nbase + 32 + lane < n) {
       nv2 = __ldcs(a.w + lo + nbase + 32 + lane);
@@ -119,12 +137,14 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
         int base = 0;
         double v = 0.0, v2 = 0.0;
         int32_t idv = 0, idv2 = 0;
+        int es = 0;  // IND: the element's offset from lo
         if (PF) {
           base = nbase;
           v = nv;
           idv = nid;
           v2 = nv2;
           idv2 = nid2;
+          es = nslot;
         } else {
           if (lane == 0) base = atomicAdd(&sh.pool, 32);
           base = __shfl_sync(FULL, base, 0);
@@ -133,25 +153,32 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
           pool_done = true;
           break;
         }
-        const int slot = base + lane, slot2 = base + 32 + lane;
+        const int slot = IND ? es : base + lane, slot2 = base + 32 + lane;
+        const bool in = base + lane < n;
         bool surv = false, surv2 = false;
         if (PF) {
           if (lane == 0) nbase = atomicAdd(&sh.pool, PB);
           nbase = __shfl_sync(FULL, nbase, 0);
           if (nbase + lane < n) {
-            nv = __ldcs(a.w + lo + nbase + lane);
-            nid = __ldcs(a.ids + lo + nbase + lane);
+            if (IND) {
+              nslot = (int)__ldcs(a.plist + lb + nbase + lane);
+              nv = __ldcs(a.w + lo + nslot);
+              nid = __ldcs(a.ids + lo + nslot);
+            } else {
+              nv = __ldcs(a.w + lo + nbase + lane);
+              nid = __ldcs(a.ids + lo + nbase + lane);
+            }
           }
           if (PB == 64 && nbase + 32 + lane < n) {
             nv2 = __ldcs(a.w + lo + nbase + 32 + lane);
             nid2 = __ldcs(a.ids + lo + nbase + 32 + lane);
           }
         }
-        if (slot < n) {
+        if (in) {
           if (!PF) v = a.w[lo + slot];
-          screen_elem(a, lo, n, slot, v, idv, !PF, Tf, kf, sh, cnt, surv);
+          screen_elem(a, lo, lb, n, slot, v, idv, !PF, Tf, kf, sh, cnt, surv);
         }
-        if (PB == 64 && slot2 < n) screen_elem(a, lo, n, slot2, v2, idv2, false, Tf, kf, sh, cnt, surv2);
+        if (PB == 64 && slot2 < n) screen_elem(a, lo, lb, n, slot2, v2, idv2, false, Tf, kf, sh, cnt, surv2);
         const uint32_t sm = __ballot_sync(FULL, surv);
         if (surv) {  // one reciprocal per screening batch, not one per lane refill
           const int p = __popc(sm & lanemask_lt());
@@ -234,7 +261,7 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
       }
     }
     if (overflow) {  // restart this element on an 8-lane segment (updates are idempotent)
-      a.list[lo + atomicAdd(&sh.hcount, 1)] = (uint32_t)e | TAG_MEDIUM;
+      a.list[lb + atomicAdd(&sh.hcount, 1)] = (uint32_t)e | TAG_MEDIUM;
       e = -1;
       continue;
     }
@@ -396,17 +423,19 @@ __device__ __forceinline__ void clk_add(Counters&, int which, long long& t) {
 // saved 2 % of the arrivals and cost more in barriers: measured and dropped.)
 // BUDGET: FastSearch's release of budget bR (row sum bsum) instead of the bound.
 template <int ARITH, bool BUDGET = false>
-__device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, int n, uint64_t Tbits, Reg* regs,
-                                            uint32_t* area, uint16_t* dense, SmemScalars& sh, Counters& cnt,
-                                            bool& gave_up, long long& t, double bR = 0.0, double bsum = 0.0) {
+// Elements are offsets from lo; the unit's work list and promotions are at lb.
+__device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, int64_t lb, int n, uint64_t Tbits,
+                                            Reg* regs, uint32_t* area, uint16_t* dense, SmemScalars& sh,
+                                            Counters& cnt, bool& gave_up, long long& t, double bR = 0.0,
+                                            double bsum = 0.0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nh = sh.hcount, nb = sh.bcount;
-  uint32_t* back = a.list + lo + n - nb;  // the 32-lane and dense entries
+  uint32_t* back = a.list + lb + n - nb;  // the 32-lane and dense entries
   {
     const int seg = lane / MED_SW;
     const HashPiN<MED_SLOTS> hp{area + (warp * (32 / MED_SW) + seg) * MED_SLOTS};
-    seg_phase<ARITH, MED_SW, HashPiN<MED_SLOTS>, BUDGET>(a, lo, Tbits, regs, a.list + lo, nh, &sh.c_med, TAG_MEDIUM, hp, MED_MAX_FILL,
-                             a.plist + lo, &sh.pcount, cnt, gave_up, bR, bsum);
+    seg_phase<ARITH, MED_SW, HashPiN<MED_SLOTS>, BUDGET>(a, lo, Tbits, regs, a.list + lb, nh, &sh.c_med, TAG_MEDIUM, hp, MED_MAX_FILL,
+                             a.plist + lb, &sh.pcount, cnt, gave_up, bR, bsum);
   }
   clk_add(cnt, CLK_MEDIUM, t);
   // a warp's hash region is the same in both phases: the heavy list needs no barrier
@@ -420,7 +449,7 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, int
   clk_add(cnt, CLK_WAIT, t);
   {
     const HashPi hp{area + warp * HASH_SLOTS};
-    seg_phase<ARITH, 32, HashPi, BUDGET>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_pheavy, TAG_HEAVY, hp, HASH_MAX_FILL,
+    seg_phase<ARITH, 32, HashPi, BUDGET>(a, lo, Tbits, regs, a.plist + lb, sh.pcount, &sh.c_pheavy, TAG_HEAVY, hp, HASH_MAX_FILL,
                          nullptr, nullptr, cnt, gave_up, bR, bsum);
   }
   clk_add(cnt, CLK_HEAVY, t);
@@ -434,7 +463,7 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, int
     const DensePi dp{mine};
     seg_phase<ARITH, 32, DensePi, BUDGET>(a, lo, Tbits, regs, back, nb, &sh.c_super, TAG_SUPER, dp, 1 << 30, nullptr, nullptr, cnt,
                          gave_up, bR, bsum);
-    seg_phase<ARITH, 32, DensePi, BUDGET>(a, lo, Tbits, regs, a.plist + lo, sh.pcount, &sh.c_psuper, TAG_SUPER, dp, 1 << 30,
+    seg_phase<ARITH, 32, DensePi, BUDGET>(a, lo, Tbits, regs, a.plist + lb, sh.pcount, &sh.c_psuper, TAG_SUPER, dp, 1 << 30,
                          nullptr, nullptr, cnt, gave_up, bR, bsum);
   }
   clk_add(cnt, CLK_SUPER, t);
@@ -522,12 +551,12 @@ __device__ __forceinline__ void fastgm_row(const SketchArgs& a, int row, int64_t
     reset_lists(sh);
     __syncthreads();
     clk_add(cnt, CLK_SETUP, t);
-    light_phase<ARITH, false>(a, lo, n, Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt,
+    light_phase<ARITH, false>(a, lo, lo, n, Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt,
                               gave_up);
     clk_add(cnt, CLK_LIGHT, t);
     __syncthreads();
     clk_add(cnt, CLK_WAIT, t);
-    warp_phases<ARITH>(a, lo, n, Tbits, regs, area, dense, sh, cnt, gave_up, t);
+    warp_phases<ARITH>(a, lo, lo, n, Tbits, regs, area, dense, sh, cnt, gave_up, t);
     // a register above T may still be lowered by an arrival above T: redo wider.
     // (Without a starting sketch that is exactly an unfilled register.)
     int empty = 0;
@@ -636,7 +665,7 @@ __device__ __forceinline__ void fastsearch_row(const SketchArgs& a, int row, int
       budget_light_phase<ARITH>(a, lo, n, bR, bRprev, dsum, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt,
                                 gave_up);
       __syncthreads();
-      warp_phases<ARITH, true>(a, lo, n, DBL_MAX_BITS, regs, area, dense, sh, cnt, gave_up, t, bR, dsum);
+      warp_phases<ARITH, true>(a, lo, lo, n, DBL_MAX_BITS, regs, area, dense, sh, cnt, gave_up, t, bR, dsum);
       rounds = r;
       int empty = 0;
       for (int j = tid; j < a.k; j += BLOCK) empty |= (regs[j].y == INF_BITS);
@@ -660,9 +689,9 @@ __device__ __forceinline__ void fastsearch_row(const SketchArgs& a, int row, int
       const float Tf = fmaxf(__double2float_ru(__longlong_as_double((long long)m)), 1.17549435e-38f);
       reset_lists(sh);
       __syncthreads();
-      light_phase<ARITH, false>(a, lo, n, m, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt, gave_up);
+      light_phase<ARITH, false>(a, lo, lo, n, m, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt, gave_up);
       __syncthreads();
-      warp_phases<ARITH>(a, lo, n, m, regs, area, dense, sh, cnt, gave_up, t);
+      warp_phases<ARITH>(a, lo, lo, n, m, regs, area, dense, sh, cnt, gave_up, t);
     }
   }
   write_out(a, row, regs);
@@ -675,18 +704,135 @@ __device__ __forceinline__ void fastsearch_row(const SketchArgs& a, int row, int
 // One chunk of a long row: its elements with the bound from the row's sum (or,
 // in the bound-free mode, a ladder of passes on the chunk's own registers), then
 // its registers merged into the row's global ones.
+// One element's arrival stream by the whole CTA (Sec. 2.2; a super-heavy element
+// of a compacted long row, whose stream would otherwise be one warp's long serial
+// chain): rounds of BLOCK consecutive arrivals, each thread one arrival's term and
+// RandInt target in parallel; the exact prefix sums by warp scans and a scan of
+// the warps' totals (carried across rounds); the arrivals up to the first above T
+// kept (times ascend, so they are a prefix); their Fisher-Yates steps on a dense
+// permutation by warp 0, 32 steps at a time in order; then each thread lowers its
+// arrival's register.  Block-wide.  Scratch: area (targets, servers, warp
+// totals), pi (k entries).
 template <int ARITH>
+__device__ __forceinline__ void coop_stream(const SketchArgs& a, int64_t lo, uint32_t slot, uint64_t Tbits, Reg* regs,
+                                         uint32_t* area, uint16_t* pi, Counters& cnt, bool& gave_up) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = a.k;
+  uint16_t* Jb = reinterpret_cast<uint16_t*>(area);             // BLOCK targets
+  uint16_t* cb = Jb + BLOCK;                                      // BLOCK servers
+  Fix* tot = reinterpret_cast<Fix*>(area + BLOCK);                // WARPS totals, then offsets; [WARPS]: carry
+  const int32_t id = a.ids[lo + slot];
+  const double R = arr_rcp<ARITH>(a.w[lo + slot]);
+  const DensePi dp{pi};
+  dp.reset_seg(k, tid, BLOCK);
+  if (tid == 0) tot[WARPS] = fix_zero();
+  __syncthreads();
+  for (int z0 = 0; z0 < k; z0 += BLOCK) {
+    const int z = z0 + tid;
+    Fix f = fix_zero();
+    int J = z;
+    if (z < k) f = arrival_term<ARITH>(id, z, k, a.key0, a.key1, a.ctab, J);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      Fix g;
+      g.w0 = __shfl_up_sync(FULL, f.w0, d);
+      g.w1 = __shfl_up_sync(FULL, f.w1, d);
+      if (lane >= d) fix_add(f, g);
+    }
+    if (lane == 31) tot[warp] = f;
+    Jb[tid] = (uint16_t)(z < k ? J : 0);
+    __syncthreads();
+    if (warp == 0) {  // offsets of the warps: the carry plus the exclusive scan of their totals
+      Fix x = lane < WARPS ? tot[lane] : fix_zero();
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        Fix g;
+        g.w0 = __shfl_up_sync(FULL, x.w0, d);
+        g.w1 = __shfl_up_sync(FULL, x.w1, d);
+        if (lane >= d) fix_add(x, g);
+      }
+      Fix e;  // exclusive: the lane below's inclusive sum
+      e.w0 = __shfl_up_sync(FULL, x.w0, 1);
+      e.w1 = __shfl_up_sync(FULL, x.w1, 1);
+      if (lane == 0) e = fix_zero();
+      const Fix c = tot[WARPS];
+      fix_add(e, c);
+      __syncwarp();
+      if (lane < WARPS) tot[lane] = e;
+    }
+    __syncthreads();
+    fix_add(f, tot[warp]);  // the exact prefix sum through arrival z
+    const uint64_t bb = z < k ? (uint64_t)__double_as_longlong(arr_mul<ARITH>(fix_round(f), R)) : ~0ull;
+    const bool keep = bb <= Tbits;
+    const int nk = __syncthreads_count(keep);
+    if (tid == BLOCK - 1) tot[WARPS] = f;  // the next round's carry (read after the barriers below)
+    if (warp == 0) {  // Fisher-Yates steps z0 .. z0 + nk - 1, in order
+      for (int s0 = 0; s0 < nk; s0 += 32) {
+        const int n = min(32, nk - s0);
+        const int Jl = lane < n ? (int)Jb[s0 + lane] : z0 + s0 + lane;
+        int c;
+        seg_fy_steps<32>(dp, z0 + s0, Jl, n, lane, c);
+        if (lane < n) cb[s0 + lane] = (uint16_t)c;
+      }
+    }
+    __syncthreads();
+    if (keep) {
+      cnt.cas += reg_lower(smem_addr(&regs[cb[tid]]), bb, (uint64_t)(uint32_t)id, gave_up);
+      ++cnt.kept;
+    }
+    if (tid == 0) cnt.arrivals += (uint32_t)min(BLOCK, k - z0);
+    __syncthreads();  // Jb, cb and the totals are reused
+    if (nk < BLOCK) break;
+  }
+  if (tid == 0) ++cnt.heavy;
+}
+
+// CMP: compiled with the compacted units (taken when the launch compacted its
+// long rows, a.compact).
+template <int ARITH, bool CMP>
 __device__ __forceinline__
 void chunk_unit(const SketchArgs& a, int row, int chunk, int longi, int64_t lo, int64_t hi, Reg* regs,
                 uint32_t* area, uint16_t* dense, unsigned char* wbuf, SmemScalars& sh, Counters& cnt,
                 bool& gave_up) {
   const int k = a.k, tid = threadIdx.x;
-  const int64_t clo = lo + (int64_t)chunk * a.chunk_len;
-  const int64_t chi = min(hi, clo + a.chunk_len);
   Reg* g = a.long_regs + (int64_t)longi * k;
+  const int nsuper = CMP && chunk < 0 ? (int)a.longs[longi].nsuper : 0;  // chunk < 0: compacted units only
+  if (CMP && chunk < 0 && -1 - chunk < nsuper) {  // a super-heavy element of a compacted row: the whole CTA
+    long long t = read_clock();
+    uint64_t Tbits;
+    float Tf;
+    chunk_bound(a, row, a.longs[longi].sum, Tbits, Tf);
+    coop_stream<ARITH>(a, lo, a.plist[hi - 1 - (-1 - chunk)], Tbits, regs, area, dense, cnt, gave_up);
+    clk_add(cnt, CLK_SUPER, t);
+    merge_to_global<BLOCK>(regs, g, k, gave_up);
+    return;
+  }
+  // A unit of heavy elements of a compacted row: entries list[hi - j1, hi - j0)
+  // on the warp paths only.  A unit of a compacted row's compact list: entries
+  // [c0, c1), offsets from lo, one pass at the row's bound.  Otherwise elements
+  // [clo, chi) of the row.
+  const bool heavy = CMP && chunk < 0, cmp = CMP && a.compact != 0;
+  int64_t clo, lb, chi;
+  if (heavy) {
+    const int64_t j0 = (int64_t)(-1 - chunk - nsuper) * HEAVY_UNIT;
+    const int64_t j1 = min((int64_t)a.longs[longi].nheavy, j0 + HEAVY_UNIT);
+    clo = lo;
+    lb = hi - j1;
+    chi = lo + j1 - j0;
+  } else if (cmp) {
+    const int64_t cu = a.hdr->cunit;
+    const int64_t c0 = (int64_t)chunk * cu;
+    clo = lo;
+    lb = lo + c0;
+    chi = lo + min((int64_t)a.longs[longi].ncomp, c0 + cu) - c0;
+  } else {
+    clo = lo + (int64_t)chunk * a.chunk_len;
+    lb = clo;
+    chi = min(hi, clo + a.chunk_len);
+  }
   if (chi > clo) {
     float tdummy;
-    const bool ladder = a.chunk_ladder && !row_bound(a, row, tdummy);
+    const bool ladder = !cmp && a.chunk_ladder && !row_bound(a, row, tdummy);
     float sumc = 0.0f;
     int nposc = 1;
     long long t = read_clock();
@@ -700,14 +846,17 @@ void chunk_unit(const SketchArgs& a, int row, int chunk, int longi, int64_t lo, 
       else
         chunk_bound(a, row, a.longs[longi].sum, Tbits, Tf);
       reset_lists(sh);
+      if (heavy && tid == 0) sh.bcount = (int)(chi - clo);  // the whole unit is its back list
       __syncthreads();
       clk_add(cnt, CLK_SETUP, t);
-      light_phase<ARITH, true>(a, clo, (int)(chi - clo), Tbits, Tf, regs, area, wbuf + (tid >> 5) * WBUF_BYTES, sh,
-                               cnt, gave_up);
-      clk_add(cnt, CLK_LIGHT, t);
-      __syncthreads();
-      clk_add(cnt, CLK_WAIT, t);
-      warp_phases<ARITH>(a, clo, (int)(chi - clo), Tbits, regs, area, dense, sh, cnt, gave_up, t);
+      if (!heavy) {
+        light_phase<ARITH, true>(a, clo, lb, (int)(chi - clo), Tbits, Tf, regs, area,
+                                 wbuf + (tid >> 5) * WBUF_BYTES, sh, cnt, gave_up, cmp);
+        clk_add(cnt, CLK_LIGHT, t);
+        __syncthreads();
+        clk_add(cnt, CLK_WAIT, t);
+      }
+      warp_phases<ARITH>(a, clo, lb, (int)(chi - clo), Tbits, regs, area, dense, sh, cnt, gave_up, t);
       if (final) break;
       // the chunk's own sketch is exact once its registers are all at or below T
       int empty = 0;
@@ -735,8 +884,8 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
   const long long t_start = read_clock();
   if ((tid & 31) == 0)
     for (int q = 0; q < NCLK; ++q) sh.clk[tid >> 5][q] = 0ull;
-  const uint32_t n_extra = a.hdr->n_extra, n_long = a.hdr->n_long;
-  const uint32_t n_units = MODE == MODE_MAIN ? n_extra + (uint32_t)a.n_rows
+  const uint32_t n_extra = a.hdr->n_extra, n_long = a.hdr->n_long, n_hu = a.hdr->n_hunits;
+  const uint32_t n_units = (MODE == MODE_MAIN || MODE == MODE_CMP) ? n_hu + n_extra + (uint32_t)a.n_rows
                            : MODE == MODE_FS ? (uint32_t)a.n_rows
                                              : a.hdr->esc_count;
 
@@ -755,7 +904,7 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
       chunk = 0;
       longi = -1;
     } else {
-      resolve_unit(a, u, n_extra, n_long, row, chunk, longi);
+      resolve_unit(a, u, n_hu, n_extra, n_long, row, chunk, longi);
     }
     int64_t lo, hi;
     row_bounds(a, row, lo, hi);
@@ -771,11 +920,13 @@ __global__ void __launch_bounds__(BLOCK, CTAS_PER_SM) fastgm_kernel(SketchArgs a
       __syncthreads();
       continue;
     }
-    const LongRow lr = a.longs[longi];
-    if (lr.npos > 0) chunk_unit<ARITH>(a, row, chunk, longi, lo, hi, regs, area, dense, wbuf, sh, cnt, gave_up);
+    if (a.longs[longi].npos > 0)
+      chunk_unit<ARITH, MODE == MODE_CMP || SHARED_CMP>(a, row, chunk, longi, lo, hi, regs, area, dense, wbuf, sh,
+                                                        cnt, gave_up);
     __threadfence();
     __syncthreads();
-    if (tid == 0) sh.last = (atomicAdd(&a.longs[longi].done, 1u) == lr.nchunks - 1) ? 1 : 0;
+    if (tid == 0)
+      sh.last = (atomicAdd(&a.longs[longi].done, 1u) == a.longs[longi].nchunks + a.longs[longi].nhunits - 1u) ? 1 : 0;
     __syncthreads();
     if (sh.last) {
       __threadfence();
@@ -809,7 +960,7 @@ __global__ void __launch_bounds__(BLOCK, 1) plain_kernel(SketchArgs a) {
     const uint32_t u = (uint32_t)sh.unit;
     if (u >= n_units) break;
     int row, chunk, longi;
-    resolve_unit(a, u, n_extra, n_long, row, chunk, longi);
+    resolve_unit(a, u, 0u, n_extra, n_long, row, chunk, longi);
     int64_t lo, hi;
     row_bounds(a, row, lo, hi);
     init_regs(a, regs, k);
@@ -937,7 +1088,22 @@ static int launch_all(SketchArgs a, bool plain, int nsm, cudaStream_t stream) {
       return GM_ECUDA;
     a.chunk_len = chunk_len_for(a.nnz, nsm * (per_sm > 0 ? per_sm : 1));
   }
-  const int max_units = a.n_rows + (int)((a.nnz + a.chunk_len - 1) / a.chunk_len) + a.max_long;
+  // Long rows with a fixed bound (closed form, learned or caller-given) are
+  // compacted: screened first by the whole grid, then sketched from their lists.
+  // The bound-free ladder grows each chunk's bound, so it keeps the element ranges.
+  // (Compact entries are offsets within the row, tagged in the work lists' top two
+  // bits: rows must stay below 2^30 elements, which nnz < 2^30 ensures.)
+  // Only batches of long rows (an average row of more than SPLIT_LEN elements)
+  // are compacted: a few long rows among many short ones overlap their chunk
+  // units with the short rows, and a Stream-FastGM chunk (one row from a running
+  // sketch, whose y* screens out most of it) gains less from a second pass over
+  // its few survivors than that pass costs.
+  a.compact = (GM_COMPACT_LONG && GM_SCREEN_PAIR == 1 && !plain && a.fs_delta == 0 && !a.chunk_ladder &&
+               !a.init_y && a.nnz < ((int64_t)1 << 30) && a.nnz > (int64_t)SPLIT_LEN * a.n_rows)
+                  ? 1
+                  : 0;
+  const int max_units = a.n_rows + (int)((a.nnz + a.chunk_len - 1) / a.chunk_len) + a.max_long +
+                        (a.compact ? (int)(a.nnz / 2048) : 0);
   if (a.fs_delta == 0) {  // FastSearch's schedule takes every row whole: no long-row plan
     plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a);
     longprep_kernel<<<nsm * 8, PREP_THREADS, 0, stream>>>(a);
@@ -962,11 +1128,30 @@ static int launch_all(SketchArgs a, bool plain, int nsm, cudaStream_t stream) {
     if (g_main_after) cudaEventRecord(g_main_after, stream);
     return GM_OK;
   }
-  rc = occupancy_grid(fastgm_kernel<ARITH, MODE_MAIN>, sm, nsm, max_units, grid);
-  if (rc != GM_OK) return rc;
-  if (g_main_before) cudaEventRecord(g_main_before, stream);
-  fastgm_kernel<ARITH, MODE_MAIN><<<grid, BLOCK, sm, stream>>>(a);
-  if (g_main_after) cudaEventRecord(g_main_after, stream);
+  bool launched = false;
+  if constexpr (!SHARED_CMP) {
+    if (a.compact) {  // the same persistent kernel, compiled with the compacted units
+      rc = occupancy_grid(fastgm_kernel<ARITH, MODE_CMP>, sm, nsm, max_units, grid);
+      if (rc != GM_OK) return rc;
+      screen_kernel<<<nsm * 8, SCREEN_THREADS, 0, stream>>>(a);
+      compact_plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a, grid);
+      if (g_main_before) cudaEventRecord(g_main_before, stream);
+      fastgm_kernel<ARITH, MODE_CMP><<<grid, BLOCK, sm, stream>>>(a);
+      if (g_main_after) cudaEventRecord(g_main_after, stream);
+      launched = true;
+    }
+  }
+  if (!launched) {
+    rc = occupancy_grid(fastgm_kernel<ARITH, MODE_MAIN>, sm, nsm, max_units, grid);
+    if (rc != GM_OK) return rc;
+    if (a.compact) {
+      screen_kernel<<<nsm * 8, SCREEN_THREADS, 0, stream>>>(a);
+      compact_plan_kernel<<<1, PLAN_THREADS, 0, stream>>>(a, grid);
+    }
+    if (g_main_before) cudaEventRecord(g_main_before, stream);
+    fastgm_kernel<ARITH, MODE_MAIN><<<grid, BLOCK, sm, stream>>>(a);
+    if (g_main_after) cudaEventRecord(g_main_after, stream);
+  }
   // the redo kernel: long rows left unfilled are rare (p = 1e-3 per row), so a
   // small grid; its empty launch then costs little
   int grid_esc = 0;

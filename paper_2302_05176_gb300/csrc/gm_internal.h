@@ -26,6 +26,8 @@ struct WsHeader {
   uint32_t esc_count;     // long rows to redo with a larger bound
   uint32_t esc_counter;   // next entry of that list
   uint32_t n_pieces;      // pre-pass pieces of all long rows
+  uint32_t n_hunits;      // compacted long rows: units of heavy and super-heavy elements (dispatched first)
+  uint32_t cunit;         // compacted long rows: entries of a compact list per chunk unit
   uint32_t pad;
   unsigned long long counters[WS_NCOUNTERS];
 };
@@ -44,7 +46,11 @@ struct LongRow {
   uint32_t piece_off;    // index of its first pre-pass piece
   uint32_t npieces;      // pieces of PIECE_LEN elements
   uint32_t pieces_done;  // pieces summed so far
-  uint32_t pad;
+  uint32_t ncomp;        // compacted mode: light and medium elements left after the first-arrival screen
+  uint32_t nsuper;       // compacted mode: super-heavy elements, listed at the back of the row's plist range
+  uint32_t nheavy;       // compacted mode: heavy elements, listed at the back of the row's work list
+  uint32_t heavy_off;    // compacted mode: index of its first heavy unit
+  uint32_t nhunits;      // compacted mode: its units of heavy elements, then one per super-heavy element
 };
 
 // Sums of one pre-pass piece of a long row.

@@ -51,6 +51,15 @@ namespace gm {
 
 // Build-time knobs (overridable for experiments): light-lane map capacity, lanes
 // per medium segment and its hash table.  The CTA shapes are in gm_fastgm_shape.cuh.
+#ifndef GM_COMPACT_LONG
+#define GM_COMPACT_LONG 1  // long rows with a fixed bound: screened first, sketched from compact lists
+#endif
+#ifndef GM_COMPACT_MIN_UNIT
+#define GM_COMPACT_MIN_UNIT 8192  // fewest compact-list entries per chunk unit
+#endif
+#ifndef GM_HEAVY_UNIT
+#define GM_HEAVY_UNIT 32  // heavy elements per heavy unit
+#endif
 #ifndef GM_MAPCAP
 #define GM_MAPCAP 16
 #endif
@@ -120,6 +129,7 @@ struct SketchArgs {
   float q1, q2, q_split;  // normalised bounds: first pass, second pass, long rows (inf = none)
   float grow;             // factor of each later pass's bound over the one before (a power of two)
   int chunk_ladder;       // bound-free: long-row chunks grow their own bound, pruned by the row's y*
+  int compact;            // long rows screened first (screen_kernel): chunk units over their compact lists
   const float* t_row;     // learned first-pass bound per row (absolute), or null
   float light_max, medium_max, heavy_max;  // routing thresholds (expected arrivals below T)
   const int32_t* init_s;  // stream mode (one row): registers start from this sketch, else unfilled
@@ -389,8 +399,26 @@ __device__ __forceinline__ void merge_to_global(const Reg* regs, Reg* g, int k, 
 }
 
 // Resolve work unit u into (row, chunk, long index).
-__device__ __forceinline__ void resolve_unit(const SketchArgs& a, uint32_t u, uint32_t n_extra, uint32_t n_long,
-                                             int& row, int& chunk, int& longi) {
+// Units in dispatch order: the heavy units of compacted long rows (chunk -1 - j
+// for a row's heavy unit j), the extra chunks of long rows, then one unit per row
+// (chunk 0 of a long row).
+__device__ __forceinline__ void resolve_unit(const SketchArgs& a, uint32_t u, uint32_t n_hu, uint32_t n_extra,
+                                             uint32_t n_long, int& row, int& chunk, int& longi) {
+  if (u < n_hu) {  // a heavy unit: binary search the heavy-unit offsets
+    int lo = 0, hi = (int)n_long - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.longs[mid].heavy_off <= u)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    longi = lo;
+    row = (int)a.longs[lo].row;
+    chunk = -1 - (int)(u - a.longs[lo].heavy_off);
+    return;
+  }
+  u -= n_hu;
   if (u < n_extra) {  // an extra chunk of a long row: binary search the chunk offsets
     int lo = 0, hi = (int)n_long - 1;
     while (lo < hi) {
@@ -414,6 +442,7 @@ __device__ __forceinline__ void resolve_unit(const SketchArgs& a, uint32_t u, ui
 constexpr int MODE_MAIN = 0;
 constexpr int MODE_ESC = 1;
 constexpr int MODE_FS = 2;  // FastSearch's schedule (gm_sketch_fastsearch): every row whole, by one CTA
+constexpr int MODE_CMP = 3;  // MODE_MAIN for a launch whose long rows were compacted (screen_kernel)
 constexpr int FS_MAX_ROUNDS = 4096;  // then one last pass releases all k arrivals of every element
 
 
@@ -478,7 +507,11 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(SketchArgs a) {
         lr.piece_off = 0u;
         lr.npieces = (uint32_t)((len + PIECE_LEN - 1) / PIECE_LEN);
         lr.pieces_done = 0u;
-        lr.pad = 0u;
+        lr.ncomp = 0u;
+        lr.nsuper = 0u;
+        lr.nheavy = 0u;
+        lr.heavy_off = 0u;
+        lr.nhunits = 0u;
         a.longs[i] = lr;
       }
     }
@@ -621,6 +654,186 @@ __global__ void __launch_bounds__(PREP_THREADS) longprep_kernel(SketchArgs a) {
         a.longs[li].npos = rn;
       }
     }
+  }
+}
+
+// Compacted long rows, first step: the first-arrival screen of every element of
+// every long row by the whole grid at once (no barriers, no per-chunk registers),
+// one warp per sub-piece (a pre-pass piece cut into 1 to 16 parts, enough for
+// about two per warp of the grid), eight batches of 32 loads in flight per warp.
+// An element is kept when it is positive and either expected to need more than
+// a.light_max arrivals below the row's bound or not certainly above it at its
+// first arrival (screen_out); the others contribute nothing to the sketch
+// (Sec. 2.2, FastPrune at the first arrival).  Kept light and medium elements are
+// listed by their offset in the row at the front of the row's range of plist
+// (each warp stages up to SCREEN_BUF of them in shared memory and claims their
+// place with one atomic add); heavy ones (above a.medium_max, for the 32-lane
+// path) at the back of the row's range of list, tagged; super-heavy ones (above
+// a.heavy_max, each streamed by a whole CTA) at the back of its range of plist.  Entries come in
+// no particular order: register updates are order-free minima.  The dropped
+// positive elements and the heavy ones are counted here, the others by the chunk
+// units that screen them again.
+constexpr int SCREEN_THREADS = 256;
+constexpr int SCREEN_BUF = 256;
+#ifndef GM_SCREEN_DEPTH
+#define GM_SCREEN_DEPTH 8  // batches of 32 loads in flight per warp
+#endif
+#ifndef GM_SCREEN_MINB
+#define GM_SCREEN_MINB 4  // resident CTAs per SM the register budget is sized for
+#endif
+constexpr int SD = GM_SCREEN_DEPTH;
+// Class limits of x = v T: expected arrivals k (1 - exp(-x)) above lim <=> x > -ln(1 - lim / k).
+__device__ __forceinline__ float class_limit(float lim, float kf) {
+  return lim < kf ? -log1pf(-lim / kf) : __int_as_float(0x7F800000);
+}
+constexpr int HEAVY_UNIT = GM_HEAVY_UNIT;
+__global__ void __launch_bounds__(SCREEN_THREADS, GM_SCREEN_MINB) screen_kernel(SketchArgs a) {
+  __shared__ uint32_t buf[SCREEN_THREADS / 32][SCREEN_BUF];
+  const uint32_t n_long = a.hdr->n_long, n_pieces = a.hdr->n_pieces;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* wb = buf[warp];
+  const float kf = (float)a.k;
+  uint32_t n_elem = 0u, n_scr = 0u;
+  const uint32_t warps = gridDim.x * (SCREEN_THREADS / 32);
+  uint32_t S = 1u;
+  while (S < 16u && (uint64_t)n_pieces * S < 2ull * warps) S <<= 1;
+  const int sublen = PIECE_LEN / (int)S;
+  const uint64_t n_units = (uint64_t)n_pieces * S;
+  for (uint64_t q = (uint64_t)blockIdx.x * (SCREEN_THREADS / 32) + warp; q < n_units; q += warps) {
+    const uint32_t p = (uint32_t)(q / S), sub = (uint32_t)(q % S);
+    int lo_i = 0, hi_i = (int)n_long - 1;  // the long row owning piece p
+    while (lo_i < hi_i) {
+      const int mid = (lo_i + hi_i + 1) >> 1;
+      if (a.longs[mid].piece_off <= p)
+        lo_i = mid;
+      else
+        hi_i = mid - 1;
+    }
+    const int li = lo_i;
+    const int row = (int)a.longs[li].row;
+    if (a.longs[li].npos <= 0) continue;  // nothing to sketch in this row
+    int64_t lo, hi;
+    row_bounds(a, row, lo, hi);
+    const uint32_t off = (p - a.longs[li].piece_off) * (uint32_t)PIECE_LEN + sub * (uint32_t)sublen;
+    if (lo + off >= hi) continue;
+    const int n = (int)min((int64_t)sublen, hi - (lo + off));
+    uint64_t Tbits;
+    float Tf;
+    chunk_bound(a, row, a.longs[li].sum, Tbits, Tf);
+    // the classes by x = v T against limits taken once (routing only: the chunk
+    // units route by the expected count itself, and either way is exact)
+    const float xl = class_limit(a.light_max, kf), xm = class_limit(a.medium_max, kf),
+                xh = class_limit(a.heavy_max, kf);
+    int nb = 0;  // staged entries (warp-uniform)
+    for (int base = 0; base < n; base += SD * 32) {
+      double v[SD];
+      int32_t id[SD];
+#pragma unroll
+      for (int r = 0; r < SD; ++r) {
+        const int i = base + r * 32 + lane;
+        v[r] = i < n ? __ldcs(a.w + lo + off + i) : 0.0;
+        id[r] = i < n ? __ldcs(a.ids + lo + off + i) : 0;
+      }
+#pragma unroll
+      for (int r = 0; r < SD; ++r) {
+        const int i = base + r * 32 + lane;
+        bool keep = false;
+        if (i < n && positive_finite(v[r])) {
+          const float vf = f32_trunc(v[r]);
+          const float x = vf * Tf;
+          ++n_elem;
+          if (x > xh) {  // super-heavy: a unit of its own, dispatched first
+            a.plist[hi - 1 - atomicAdd(&a.longs[li].nsuper, 1u)] = off + (uint32_t)i;
+          } else if (x > xm) {  // heavy: units of HEAVY_UNIT, dispatched first
+            a.list[hi - 1 - atomicAdd(&a.longs[li].nheavy, 1u)] = (off + (uint32_t)i) | TAG_HEAVY;
+          } else if (x > xl) {
+            keep = true;
+          } else {
+            const Words wd = philox((uint32_t)id[r], 0u, a.key0, a.key1);
+            keep = !screen_out(wd.w1, vf, Tf, kf);
+            if (!keep) ++n_scr;
+          }
+          if (keep) --n_elem;  // counted again by its chunk unit
+        }
+        const uint32_t m = __ballot_sync(FULL, keep);
+        if (keep) wb[nb + __popc(m & lanemask_lt())] = off + (uint32_t)i;
+        nb += __popc(m);
+        if (nb > SCREEN_BUF - 32) {  // flush the staged entries
+          __syncwarp();
+          uint32_t at = 0u;
+          if (lane == 0) at = atomicAdd(&a.longs[li].ncomp, (uint32_t)nb);
+          at = __shfl_sync(FULL, at, 0);
+          for (int j = lane; j < nb; j += 32) a.plist[lo + at + j] = wb[j];
+          __syncwarp();
+          nb = 0;
+        }
+      }
+    }
+    if (nb > 0) {
+      __syncwarp();
+      uint32_t at = 0u;
+      if (lane == 0) at = atomicAdd(&a.longs[li].ncomp, (uint32_t)nb);
+      at = __shfl_sync(FULL, at, 0);
+      for (int j = lane; j < nb; j += 32) a.plist[lo + at + j] = wb[j];
+      __syncwarp();
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    n_elem += __shfl_xor_sync(FULL, n_elem, d);
+    n_scr += __shfl_xor_sync(FULL, n_scr, d);
+  }
+  if (lane == 0 && n_elem) {
+    atomicAdd(&a.hdr->counters[1], (unsigned long long)n_elem);
+    atomicAdd(&a.hdr->counters[2], (unsigned long long)n_scr);
+  }
+}
+
+// Compacted long rows, second step (one CTA): every long row's compact list cut
+// into chunk units of `cunit` entries, the same for all rows -- about two units
+// per CTA of the main kernel's `grid`, between GM_COMPACT_MIN_UNIT and 65,536
+// entries -- its super-heavy elements one unit each and its heavy list into
+// units of HEAVY_UNIT elements; the units numbered as resolve_unit reads them
+// (heavy_off, n_hunits; chunk_off, n_extra).
+__global__ void __launch_bounds__(PLAN_THREADS) compact_plan_kernel(SketchArgs a, int grid) {
+  __shared__ uint32_t part[PLAN_THREADS / 32];
+  __shared__ uint32_t carry_c, carry_h;
+  __shared__ unsigned long long total;
+  const int tid = threadIdx.x;
+  const uint32_t n_long = a.hdr->n_long;
+  if (tid == 0) {
+    carry_c = carry_h = 0u;
+    total = 0ull;
+  }
+  __syncthreads();
+  unsigned long long t = 0ull;
+  for (uint32_t i = tid; i < n_long; i += PLAN_THREADS) t += a.longs[i].ncomp;
+  atomicAdd(&total, t);
+  __syncthreads();
+  unsigned long long cu = (total + 2ull * (unsigned long long)grid - 1ull) / (2ull * (unsigned long long)grid);
+  cu = cu < GM_COMPACT_MIN_UNIT ? GM_COMPACT_MIN_UNIT : (cu > 65536ull ? 65536ull : cu);
+  for (uint32_t base = 0; base < n_long; base += PLAN_THREADS) {
+    const uint32_t i = base + tid;
+    uint32_t nc = 1u, nh = 0u;
+    if (i < n_long) {
+      const uint32_t c = a.longs[i].ncomp;
+      nc = c == 0u ? 1u : (uint32_t)((c + cu - 1ull) / cu);
+      nh = a.longs[i].nsuper + (a.longs[i].nheavy + HEAVY_UNIT - 1u) / HEAVY_UNIT;
+    }
+    const uint32_t oc = plan_scan(i < n_long ? nc - 1u : 0u, part, carry_c);
+    const uint32_t oh = plan_scan(nh, part, carry_h);
+    if (i < n_long) {
+      a.longs[i].nchunks = nc;
+      a.longs[i].chunk_off = oc;
+      a.longs[i].nhunits = nh;
+      a.longs[i].heavy_off = oh;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    a.hdr->n_extra = carry_c;
+    a.hdr->n_hunits = carry_h;
+    a.hdr->cunit = (uint32_t)cu;
   }
 }
 
@@ -1170,9 +1383,9 @@ extern "C" int gm_row_ystar(const double* y, int32_t n_rows, int32_t k, double* 
 namespace gm {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = ws_bytes(GM_NOALLOC_MAX_ROWS, GM_NOALLOC_MAX_NNZ, GM_MAX_K);
-// 10,787,584 bytes (about 10.8 MB, 10.3 MiB): two 4 MiB element lists, 2 MiB of
+// 10,788,096 bytes (about 10.8 MB, 10.3 MiB): two 4 MiB element lists, 2 MiB of
 // long-row registers, the per-row index and the small tables.
-static_assert(NOALLOC_SCRATCH_BYTES == 10787584, "the documented size of the no-alloc scratch changed");
+static_assert(NOALLOC_SCRATCH_BYTES == 10788096, "the documented size of the no-alloc scratch changed");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
