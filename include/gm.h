@@ -93,6 +93,13 @@ extern "C" {
 #define GM_BOUND_NONE (1u << 4)
 #define GM_BOUND_LEARNED (2u << 4)
 #define GM_BOUND_MASK (3u << 4)
+/* Long rows with a fixed bound (closed form, learned or a caller's) are compacted
+ * -- every element's first arrival screened by the whole GPU first, the sketch
+ * then formed from the elements left -- when the batch is large and made of long
+ * rows (more than 2^23 elements, an average row above 32,768).  This flag
+ * compacts them in any batch (not Stream-FastGM chunks, not GM_BOUND_NONE).  The
+ * registers are the same either way. */
+#define GM_FLAG_COMPACT_LONG (1u << 6)
 
 /* ---- device-side counters, read back by gm_status ------------------------- */
 typedef struct gm_stats {

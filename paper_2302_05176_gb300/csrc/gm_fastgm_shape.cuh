@@ -56,9 +56,11 @@ __host__ __device__ inline size_t plain_smem_bytes(int k) {
 // their first arrival; surv = it takes a light lane.
 // The id is loaded here when `load_id` (a batch loaded at the screen), else given.
 // `slot` is the element's offset from lo; the unit's work list starts at list + lb.
+// `passed`: the element already passed this screen at this bound (a compacted
+// row's entry), so a light one streams without testing it again.
 __device__ __forceinline__ void screen_elem(const SketchArgs& a, int64_t lo, int64_t lb, int n, int slot, double v,
                                             int32_t& idv, bool load_id, float Tf, float kf, SmemScalars& sh,
-                                            Counters& cnt, bool& surv) {
+                                            Counters& cnt, bool& surv, bool passed = false) {
   if (!positive_finite(v)) return;
   ++cnt.elements;
   const float vf = f32_trunc(v);
@@ -70,6 +72,8 @@ __device__ __forceinline__ void screen_elem(const SketchArgs& a, int64_t lo, int
       a.list[lb + n - 1 - atomicAdd(&sh.bcount, 1)] = (uint32_t)slot | (lam > a.heavy_max ? TAG_SUPER : TAG_HEAVY);
     else
       a.list[lb + atomicAdd(&sh.hcount, 1)] = (uint32_t)slot | TAG_MEDIUM;
+  } else if (passed) {
+    surv = true;
   } else {
     if (load_id) idv = a.ids[lo + slot];
     const Words wd = philox((uint32_t)idv, 0u, a.key0, a.key1);
@@ -176,7 +180,7 @@ __device__ __forceinline__ void light_phase(const SketchArgs& a, int64_t lo, int
         }
         if (in) {
           if (!PF) v = a.w[lo + slot];
-          screen_elem(a, lo, lb, n, slot, v, idv, !PF, Tf, kf, sh, cnt, surv);
+          screen_elem(a, lo, lb, n, slot, v, idv, !PF, Tf, kf, sh, cnt, surv, IND);
         }
         if (PB == 64 && slot2 < n) screen_elem(a, lo, lb, n, slot2, v2, idv2, false, Tf, kf, sh, cnt, surv2);
         const uint32_t sm = __ballot_sync(FULL, surv);
@@ -1093,13 +1097,17 @@ static int launch_all(SketchArgs a, bool plain, int nsm, cudaStream_t stream) {
   // The bound-free ladder grows each chunk's bound, so it keeps the element ranges.
   // (Compact entries are offsets within the row, tagged in the work lists' top two
   // bits: rows must stay below 2^30 elements, which nnz < 2^30 ensures.)
-  // Only batches of long rows (an average row of more than SPLIT_LEN elements)
-  // are compacted: a few long rows among many short ones overlap their chunk
-  // units with the short rows, and a Stream-FastGM chunk (one row from a running
-  // sketch, whose y* screens out most of it) gains less from a second pass over
-  // its few survivors than that pass costs.
+  // Only large batches of long rows (an average row of more than SPLIT_LEN
+  // elements, more than 2^23 elements in all) are compacted: a few long rows
+  // among many short ones overlap their chunk units with the short rows; a batch
+  // of one or two long rows has too few compacted units to fill the GPU (a
+  // serving batch with a 4.5 x 10^6-element row was slower compacted); and a
+  // Stream-FastGM chunk (one row from a running sketch, whose y* screens out most
+  // of it) gains less from a second pass over its few survivors than it costs.
   a.compact = (GM_COMPACT_LONG && GM_SCREEN_PAIR == 1 && !plain && a.fs_delta == 0 && !a.chunk_ladder &&
-               !a.init_y && a.nnz < ((int64_t)1 << 30) && a.nnz > (int64_t)SPLIT_LEN * a.n_rows)
+               !a.init_y && a.nnz < ((int64_t)1 << 30) &&
+               ((a.flags & GM_FLAG_COMPACT_LONG) ||
+                (a.nnz > ((int64_t)1 << 23) && a.nnz > (int64_t)SPLIT_LEN * a.n_rows)))
                   ? 1
                   : 0;
   const int max_units = a.n_rows + (int)((a.nnz + a.chunk_len - 1) / a.chunk_len) + a.max_long +

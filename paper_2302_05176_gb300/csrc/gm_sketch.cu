@@ -399,11 +399,15 @@ __device__ __forceinline__ void merge_to_global(const Reg* regs, Reg* g, int k, 
 }
 
 // Resolve work unit u into (row, chunk, long index).
-// Units in dispatch order: the heavy units of compacted long rows (chunk -1 - j
-// for a row's heavy unit j), the extra chunks of long rows, then one unit per row
-// (chunk 0 of a long row).
+// Units in dispatch order: the extra chunks of long rows, one unit per row
+// (chunk 0 of a long row), then the super-heavy and heavy units of compacted
+// long rows (chunk -1 - j for a row's unit j).  The compacted rows' chunk units
+// are the longest, so they go first and the shorter heavy units fill the CTAs
+// that finish early (measured on 16 x 10^6 Pareto(1.2): 0.299 against 0.317 ms
+// per call with the heavy units first).
 __device__ __forceinline__ void resolve_unit(const SketchArgs& a, uint32_t u, uint32_t n_hu, uint32_t n_extra,
                                              uint32_t n_long, int& row, int& chunk, int& longi) {
+  u = u < n_extra + (uint32_t)a.n_rows ? u + n_hu : u - (n_extra + (uint32_t)a.n_rows);
   if (u < n_hu) {  // a heavy unit: binary search the heavy-unit offsets
     int lo = 0, hi = (int)n_long - 1;
     while (lo < hi) {
@@ -739,7 +743,9 @@ __global__ void __launch_bounds__(SCREEN_THREADS, GM_SCREEN_MINB) screen_kernel(
         const int i = base + r * 32 + lane;
         bool keep = false;
         if (i < n && positive_finite(v[r])) {
-          const float vf = f32_trunc(v[r]);
+          // the FP64 pipe is idle here: one truncating conversion there, equal to
+          // f32_trunc(v) in FP32's normal range (outside it neither test decides)
+          const float vf = __double2float_rz(v[r]);
           const float x = vf * Tf;
           ++n_elem;
           if (x > xh) {  // super-heavy: a unit of its own, dispatched first

@@ -18,6 +18,7 @@ GM_FLAG_VALIDATE = 1 << 0
 GM_FLAG_FP64_UNIT = 1 << 2
 GM_FLAG_INT_PRODUCTS = 1 << 1
 GM_FLAG_TIGHT_BOUND = 1 << 3
+GM_FLAG_COMPACT_LONG = 1 << 6
 GM_BOUND_CLOSED = 0 << 4
 GM_BOUND_NONE = 1 << 4
 GM_BOUND_LEARNED = 2 << 4

@@ -138,23 +138,25 @@ def test_wide_shape_long_rows_and_escalations(tight):
 
 @pytest.mark.parametrize("tight", [0, gm.GM_FLAG_TIGHT_BOUND])
 def test_compacted_long_rows_against_oracle(tight):
-    """A batch of long rows only (an average row above 32,768 elements): screened
-    first by the whole grid, then sketched from the compact lists of the elements
-    left; with a tight bound also redone whole.  Against the oracle at k = 128."""
+    """Long rows compacted (GM_FLAG_COMPACT_LONG: this batch is below the size at
+    which they are by default): screened first by the whole grid, then sketched
+    from the compact lists of the elements left; with a tight bound also redone
+    whole.  Against the oracle at k = 128."""
     rng = np.random.default_rng(29)
     rows = []
     for n in (70_000, 33_000, 40_000):
         ids = np.sort(rng.choice(1 << 24, size=n, replace=False)).astype(np.int32)
         rows.append((ids, W.pareto_weights(rng, n, 1.2, 1e-3)))
     X = W.from_rows(rows)
-    outs = check(X, 128, 9, flags=gm.GM_FLAG_VALIDATE | tight, variants=("fastgm", "plain"))
+    outs = check(X, 128, 9, flags=gm.GM_FLAG_VALIDATE | gm.GM_FLAG_COMPACT_LONG | tight,
+                 variants=("fastgm", "plain"))
     assert outs["fastgm"][2]["arrivals"] < 0.1 * outs["plain"][2]["arrivals"]
 
 
 @pytest.mark.parametrize("k", [1024, 4096])
 def test_long_rows_heavy_and_super_heavy_elements(k):
-    """Long rows (screened first by the whole grid, then sketched from their compact
-    lists) with planted elements whose expected arrivals below the bound exceed
+    """Long rows compacted (screened first by the whole grid, then sketched from
+    their compact lists; GM_FLAG_COMPACT_LONG) with planted elements whose expected arrivals below the bound exceed
     the heavy threshold (units of 32 on the 32-lane path) and the super-heavy one
     (an element streamed by a whole CTA, up to all k arrivals), against the oracle
     and bit for bit against the plain sketch."""
@@ -169,8 +171,10 @@ def test_long_rows_heavy_and_super_heavy_elements(k):
         w[pos[4:]] = total * rng.uniform(0.004, 0.01, size=8)   # heavy: about 60 to 250 arrivals
         rows.append((ids, w))
     X = W.from_rows(rows)
-    s0, y0, st0 = run(gm.gm_sketch, X, k, 7)
+    s0, y0, st0 = run(gm.gm_sketch, X, k, 7, flags=gm.GM_FLAG_VALIDATE | gm.GM_FLAG_COMPACT_LONG)
     s1, y1, _ = run(gm.gm_sketch_plain, X, k, 7)
+    s2, y2, _ = run(gm.gm_sketch, X, k, 7)  # the element ranges (the batch is small)
+    assert np.array_equal(s0, s2) and np.array_equal(y0.view(np.int64), y2.view(np.int64))
     assert np.array_equal(s0, s1) and np.array_equal(y0.view(np.int64), y1.view(np.int64))
     s_ref, y_ref, y2_ref, s2_ref = oracle.sketch_rows_parallel(X.row_ptr, X.ids, X.w, k, 7,
                                                                np.arange(X.n_rows), runner_up=True)
