@@ -428,10 +428,13 @@ __device__ __forceinline__ void clk_add(Counters&, int which, long long& t) {
 // BUDGET: FastSearch's release of budget bR (row sum bsum) instead of the bound.
 template <int ARITH, bool BUDGET = false>
 // Elements are offsets from lo; the unit's work list and promotions are at lb.
+// promote: 8-lane elements that outgrow their table move to the promotion list
+// at plist + lb; otherwise they are retagged for the dense path in place (a
+// compacted row's warp-path unit, whose plist range holds other entries).
 __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, int64_t lb, int n, uint64_t Tbits,
                                             Reg* regs, uint32_t* area, uint16_t* dense, SmemScalars& sh,
                                             Counters& cnt, bool& gave_up, long long& t, double bR = 0.0,
-                                            double bsum = 0.0) {
+                                            double bsum = 0.0, bool promote = true) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nh = sh.hcount, nb = sh.bcount;
   uint32_t* back = a.list + lb + n - nb;  // the 32-lane and dense entries
@@ -439,7 +442,7 @@ __device__ __forceinline__ void warp_phases(const SketchArgs& a, int64_t lo, int
     const int seg = lane / MED_SW;
     const HashPiN<MED_SLOTS> hp{area + (warp * (32 / MED_SW) + seg) * MED_SLOTS};
     seg_phase<ARITH, MED_SW, HashPiN<MED_SLOTS>, BUDGET>(a, lo, Tbits, regs, a.list + lb, nh, &sh.c_med, TAG_MEDIUM, hp, MED_MAX_FILL,
-                             a.plist + lb, &sh.pcount, cnt, gave_up, bR, bsum);
+                             promote ? a.plist + lb : nullptr, &sh.pcount, cnt, gave_up, bR, bsum);
   }
   clk_add(cnt, CLK_MEDIUM, t);
   // a warp's hash region is the same in both phases: the heavy list needs no barrier
@@ -850,7 +853,10 @@ void chunk_unit(const SketchArgs& a, int row, int chunk, int longi, int64_t lo, 
       else
         chunk_bound(a, row, a.longs[longi].sum, Tbits, Tf);
       reset_lists(sh);
-      if (heavy && tid == 0) sh.bcount = (int)(chi - clo);  // the whole unit is its back list
+      if (heavy && tid == 0) {  // the whole unit is both its front (8-lane) and back (32-lane) list
+        sh.bcount = (int)(chi - clo);
+        sh.hcount = GM_SPLIT_MEDIUM ? (int)(chi - clo) : 0;
+      }
       __syncthreads();
       clk_add(cnt, CLK_SETUP, t);
       if (!heavy) {
@@ -860,7 +866,8 @@ void chunk_unit(const SketchArgs& a, int row, int chunk, int longi, int64_t lo, 
         __syncthreads();
         clk_add(cnt, CLK_WAIT, t);
       }
-      warp_phases<ARITH>(a, clo, lb, (int)(chi - clo), Tbits, regs, area, dense, sh, cnt, gave_up, t);
+      warp_phases<ARITH>(a, clo, lb, (int)(chi - clo), Tbits, regs, area, dense, sh, cnt, gave_up, t, 0.0, 0.0,
+                         !heavy);
       if (final) break;
       // the chunk's own sketch is exact once its registers are all at or below T
       int empty = 0;

@@ -57,8 +57,11 @@ namespace gm {
 #ifndef GM_COMPACT_MIN_UNIT
 #define GM_COMPACT_MIN_UNIT 8192  // fewest compact-list entries per chunk unit
 #endif
+#ifndef GM_SPLIT_MEDIUM
+#define GM_SPLIT_MEDIUM 1  // compacted rows: medium elements go to the warp-path units, not the chunk units
+#endif
 #ifndef GM_HEAVY_UNIT
-#define GM_HEAVY_UNIT 32  // heavy elements per heavy unit
+#define GM_HEAVY_UNIT 128  // warp-path elements per warp-path unit (the 8-lane segments of a 1024-thread CTA)
 #endif
 #ifndef GM_MAPCAP
 #define GM_MAPCAP 16
@@ -668,15 +671,16 @@ __global__ void __launch_bounds__(PREP_THREADS) longprep_kernel(SketchArgs a) {
 // An element is kept when it is positive and either expected to need more than
 // a.light_max arrivals below the row's bound or not certainly above it at its
 // first arrival (screen_out); the others contribute nothing to the sketch
-// (Sec. 2.2, FastPrune at the first arrival).  Kept light and medium elements are
-// listed by their offset in the row at the front of the row's range of plist
-// (each warp stages up to SCREEN_BUF of them in shared memory and claims their
-// place with one atomic add); heavy ones (above a.medium_max, for the 32-lane
-// path) at the back of the row's range of list, tagged; super-heavy ones (above
-// a.heavy_max, each streamed by a whole CTA) at the back of its range of plist.  Entries come in
+// (Sec. 2.2, FastPrune at the first arrival).  Kept light elements are listed by
+// their offset in the row at the front of the row's range of plist (each warp
+// stages up to SCREEN_BUF of them in shared memory and claims their place with
+// one atomic add); medium and heavy ones (above a.light_max, for the 8-lane and
+// 32-lane paths) at the back of the row's range of list, tagged; super-heavy ones
+// (above a.heavy_max, each streamed by a whole CTA) at the back of its range of
+// plist.  Entries come in
 // no particular order: register updates are order-free minima.  The dropped
-// positive elements and the heavy ones are counted here, the others by the chunk
-// units that screen them again.
+// positive elements and the medium and heavy ones are counted here, the light
+// ones by the chunk units that stream them.
 constexpr int SCREEN_THREADS = 256;
 constexpr int SCREEN_BUF = 256;
 #ifndef GM_SCREEN_DEPTH
@@ -753,13 +757,16 @@ __global__ void __launch_bounds__(SCREEN_THREADS, GM_SCREEN_MINB) screen_kernel(
           } else if (x > xm) {  // heavy: units of HEAVY_UNIT, dispatched first
             a.list[hi - 1 - atomicAdd(&a.longs[li].nheavy, 1u)] = (off + (uint32_t)i) | TAG_HEAVY;
           } else if (x > xl) {
-            keep = true;
+            if (GM_SPLIT_MEDIUM)
+              a.list[hi - 1 - atomicAdd(&a.longs[li].nheavy, 1u)] = (off + (uint32_t)i) | TAG_MEDIUM;
+            else
+              keep = true;
           } else {
             const Words wd = philox((uint32_t)id[r], 0u, a.key0, a.key1);
             keep = !screen_out(wd.w1, vf, Tf, kf);
             if (!keep) ++n_scr;
           }
-          if (keep) --n_elem;  // counted again by its chunk unit
+          if (keep) --n_elem;  // counted by its chunk unit
         }
         const uint32_t m = __ballot_sync(FULL, keep);
         if (keep) wb[nb + __popc(m & lanemask_lt())] = off + (uint32_t)i;

@@ -157,7 +157,7 @@ def test_compacted_long_rows_against_oracle(tight):
 def test_long_rows_heavy_and_super_heavy_elements(k):
     """Long rows compacted (screened first by the whole grid, then sketched from
     their compact lists; GM_FLAG_COMPACT_LONG) with planted elements whose expected arrivals below the bound exceed
-    the heavy threshold (units of 32 on the 32-lane path) and the super-heavy one
+    the heavy threshold (warp-path units, with the medium ones) and the super-heavy one
     (an element streamed by a whole CTA, up to all k arrivals), against the oracle
     and bit for bit against the plain sketch."""
     rng = np.random.default_rng(59 + k)
