@@ -52,12 +52,12 @@ def _p(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def _run_noalloc(fn, X, k, seed):
+def _run_noalloc(fn, X, k, seed, flags=0):
     rp, ids, w = gm.to_device(X)
     s = torch.full((X.n_rows, k), -7, dtype=torch.int32, device="cuda")
     y = torch.full((X.n_rows, k), -7.0, dtype=torch.float64, device="cuda")
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    rc = fn(_p(rp), _p(ids), _p(w), X.n_rows, X.nnz, k, seed, 0, _p(s), _p(y), stream)
+    rc = fn(_p(rp), _p(ids), _p(w), X.n_rows, X.nnz, k, seed, flags, _p(s), _p(y), stream)
     assert rc == 0, gm.strerror(rc)
     torch.cuda.synchronize()
     return s.cpu().numpy(), y.cpu().numpy()
@@ -75,12 +75,15 @@ def test_noalloc_matches_gm_sketch_twice(noalloc, noalloc_status):
     rng = np.random.default_rng(23)
     long_row = [(np.sort(rng.choice(1 << 24, size=n, replace=False)).astype(np.int32),
                  W.pareto_weights(rng, n, 1.2, 1e-3)) for n in (100_000, 3, 1500)]
-    cases = [(W.lognormal_batch(seed=21, n_rows=48, median=500.0, hi=6000), 1024, 7),
-             (W.uniform_rows(seed=22, n_rows=9, n_pos=[0, 1, 40, 300, 2500, 7, 64, 1000, 3]), 256, 8),
-             (W.from_rows(long_row), 4096, 9)]
+    # the last call compacts its long row (GM_FLAG_COMPACT_LONG: the row's survivor
+    # lists and unit counts live in the same scratch)
+    cases = [(W.lognormal_batch(seed=21, n_rows=48, median=500.0, hi=6000), 1024, 7, 0),
+             (W.uniform_rows(seed=22, n_rows=9, n_pos=[0, 1, 40, 300, 2500, 7, 64, 1000, 3]), 256, 8, 0),
+             (W.from_rows(long_row), 4096, 9, 0),
+             (W.from_rows(long_row), 4096, 9, gm.GM_FLAG_COMPACT_LONG)]
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for X, k, seed in cases:  # calls in a row through the shared scratch
-        s, y = _run_noalloc(noalloc, X, k, seed)
+    for X, k, seed, flags in cases:  # calls in a row through the shared scratch
+        s, y = _run_noalloc(noalloc, X, k, seed, flags)
         st = gm.gm_stats()
         assert noalloc_status(ctypes.byref(st), stream) == gm.GM_OK
         # the counters are this call's: every positive element visited at least once
