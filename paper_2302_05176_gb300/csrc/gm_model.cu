@@ -151,47 +151,6 @@ __device__ __forceinline__ int weight_bin(uint64_t bits) {
   return b < BIN_MIN ? BIN_MIN : (b > BIN_MIN + NBINS - 1 ? BIN_MIN + NBINS - 1 : b);
 }
 
-// Sum of positive doubles in FP32 with a running power-of-two scale: the sum is
-// (s - c) 2^(e - 1023), s a Kahan sum, c its compensation, e the largest biased
-// exponent seen.  Each term is its double rounded to 24 bits and scaled from the
-// bits (no FP64 instruction per element); terms below 2^-126 of the largest are
-// dropped.  Relative error about 2^-24: ample for an FP32 feature.
-struct ScaledSum {
-  int e;
-  float s, c;
-};
-__device__ __forceinline__ float pow2f(int d) { return d < -126 ? 0.0f : __int_as_float((d + 127) << 23); }
-__device__ __forceinline__ void ssum_add(ScaledSum& a, uint64_t bits) {
-  int e = (int)(bits >> 52);
-  uint64_t f = bits & 0x000FFFFFFFFFFFFFull;
-  if (e == 0) {  // subnormal: normalise the fraction
-    const int sh = __clzll((long long)f) - 11;
-    f = (f << sh) & 0x000FFFFFFFFFFFFFull;
-    e = 1 - sh;
-  }
-  uint32_t m = (uint32_t)(f >> 29) + (uint32_t)((f >> 28) & 1ull);  // 23 fraction bits, rounded
-  if (m >> 23) {  // rounding carried into the exponent
-    m = 0u;
-    ++e;
-  }
-  if (e > a.e) {
-    const float sc = pow2f(a.e - e);
-    a.s *= sc;
-    a.c *= sc;
-    a.e = e;
-  }
-  const int d = e - a.e;
-  if (d < -126) return;
-  const float t = __int_as_float(((d + 127) << 23) | (int)m);
-  const float y = t - a.c;
-  const float u = a.s + y;
-  a.c = (u - a.s) - y;
-  a.s = u;
-}
-__device__ __forceinline__ double ssum_value(const ScaledSum& a) {
-  return a.e < -100000 ? 0.0 : ldexp((double)(a.s - a.c), a.e - 1023);
-}
-
 struct FeatSmem {
   int hist[NW][NBINS];  // one histogram per warp: a warp's own row, or a share of a long row
   float feat[NW][F];
@@ -204,9 +163,10 @@ struct FeatSmem {
 
 // Accumulate elements [lo, hi) with stride `stride` from `first` into (np, sum,
 // max bits, histogram); eight loads in flight per thread (a warp streaming a row
-// alone waits on HBM latency once per eight elements per lane).
+// alone waits on HBM latency once per eight elements per lane).  The sum is in
+// FP64: one add per element on the FP64 pipe, which nothing else here uses.
 __device__ __forceinline__ void feat_scan(const double* __restrict__ w, int64_t first, int64_t hi, int stride,
-                                          int* hist, int& np, ScaledSum& acc, uint64_t& mxb) {
+                                          int* hist, int& np, double& acc, uint64_t& mxb) {
   constexpr int U = 8;
   for (int64_t base = first; base < hi; base += (int64_t)U * stride) {
     double v[U];
@@ -220,7 +180,7 @@ __device__ __forceinline__ void feat_scan(const double* __restrict__ w, int64_t 
       const uint64_t b = (uint64_t)__double_as_longlong(v[u]);
       if (b > 0ull && b < INF_BITS) {  // positive and finite
         ++np;
-        ssum_add(acc, b);
+        acc += v[u];
         mxb = b > mxb ? b : mxb;
         atomicAdd(&hist[weight_bin(b) - BIN_MIN], 1);
       }
@@ -296,10 +256,10 @@ __device__ __forceinline__ void warp_row_stats(const double* __restrict__ w, int
   for (int b = lane; b < NBINS; b += 32) hist[b] = 0;
   __syncwarp();
   np = 0;
-  ScaledSum acc{-1000000, 0.0f, 0.0f};
+  double acc = 0.0;
   mxb = 0ull;
   feat_scan(w, lo + lane, hi, 32, hist, np, acc, mxb);
-  sum = ssum_value(acc);
+  sum = acc;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
     np += __shfl_xor_sync(FULL, np, d);
@@ -328,10 +288,10 @@ __device__ void block_row_features(const double* __restrict__ w, int64_t lo, int
   for (int b = tid; b < NW * NBINS; b += NT) (&sm.hist[0][0])[b] = 0;
   __syncthreads();
   int np = 0;
-  ScaledSum acc{-1000000, 0.0f, 0.0f};
+  double acc = 0.0;
   uint64_t mxb = 0ull;
   feat_scan(w, lo + tid, hi, NT, sm.hist[warp], np, acc, mxb);
-  double sum = ssum_value(acc);
+  double sum = acc;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
     np += __shfl_xor_sync(FULL, np, d);
@@ -586,10 +546,10 @@ __global__ void __launch_bounds__(NT) learned_piece_kernel(const int64_t* row_pt
     for (int b = lane; b < NBINS; b += 32) h[b] = 0;
     __syncwarp();
     int np = 0;
-    ScaledSum acc{-1000000, 0.0f, 0.0f};
+    double acc = 0.0;
     uint64_t mxb = 0ull;
     feat_scan(w, plo + lane, phi, 32, h, np, acc, mxb);
-    double sum = ssum_value(acc);
+    double sum = acc;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
       np += __shfl_xor_sync(FULL, np, d);
