@@ -168,6 +168,11 @@ def test_learned_sketch_exact_for_any_model(k):
         assert torch.equal(s, s0) and torch.equal(y.view(torch.int64), y0.view(torch.int64)), (margin,)
         if margin == -30.0:
             assert st["rows_fallback"] == 6  # every row with a positive weight falls back (2 long)
+        # the long rows compacted at the learned bound (screened by it first): the same registers
+        s, y, ws = gm.gm_sketch_learned(rp, ids, w, k, 77, params, margin,
+                                        flags=gm.GM_FLAG_VALIDATE | gm.GM_FLAG_COMPACT_LONG)
+        assert gm.gm_status(ws)[0] == gm.GM_OK
+        assert torch.equal(s, s0) and torch.equal(y.view(torch.int64), y0.view(torch.int64)), ("compact", margin)
     # and against the oracle on the short rows
     s_ref, y_ref, y2_ref, s2_ref = oracle.sketch_rows_parallel(X.row_ptr, X.ids, X.w, k, 77,
                                                                np.array([1, 2, 5, 6]), runner_up=True)
