@@ -92,3 +92,26 @@ def test_host_side_workspace_sizes(libgm):
     lb.restype = ctypes.c_size_t
     assert 0 < lb(10, 1000) < lb(10, 1_000_000) and lb(10, 1000) < lb(100_000, 1000)
     assert lb(-1, 10) == 0 and lb(10, -1) == 0
+
+
+def header_constants():
+    """The integer #defines of include/gm.h (plain numbers and shifts), by name."""
+    text = open(os.path.join(ROOT, "include", "gm.h")).read()
+    out = {}
+    for m in re.finditer(r"^#define (GM_[A-Z0-9_]+)\s+(\(?\s*\d+u?\s*(?:<<\s*\d+)?\s*\)?)", text, flags=re.M):
+        expr = m.group(2).replace("u", "")
+        out[m.group(1)] = eval(expr, {"__builtins__": {}})
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """Every status code, flag and size the Python binding names has the header's value."""
+    from paper_2302_05176_gb300 import gm
+    consts = header_constants()
+    assert "GM_FLAG_COMPACT_LONG" in consts and "GM_BOUND_LEARNED" in consts
+    checked = 0
+    for name, value in consts.items():
+        if hasattr(gm, name):
+            assert getattr(gm, name) == value, name
+            checked += 1
+    assert checked >= 14
